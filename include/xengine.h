@@ -1,0 +1,161 @@
+/*
+ * xengine.h -- C ABI of the GB300 4-bit X-engine.
+ *
+ * The library computes, for every frequency band f and every pair of input
+ * elements i <= j (autocorrelations included), the exact integer visibility
+ *
+ *     V[f,i,j] = sum_t x[t,f,i] * conj(x[t,f,j])
+ *     Re = sum_t xr_i xr_j + xi_i xi_j,   Im = sum_t xi_i xr_j - xr_i xi_j
+ *
+ * (Eq. 1 of the paper, Sec. II.A, with X = element i and Y = element j,
+ * accumulated over time samples as Sec. II.A describes; only the upper
+ * triangle is formed because the matrix is Hermitian, Eq. 2).
+ *
+ * Input layout (Sec. III, Fig. 2): uint8 x[T][F][N], one byte per complex
+ * sample, time outermost, then band, then element. Each part is an excess-8
+ * 4-bit integer: value = nibble - 8 in [-8, 7]. The high nibble holds the
+ * real part and the low nibble the imaginary part (the paper says only that
+ * both share one byte; this is the reading the library fixes).
+ *
+ * Output layout (the paper leaves the final layout open; this is the
+ * library's): int32 V[F][B][2] with B = N(N+1)/2, bands outermost, (Re, Im)
+ * interleaved, entries row-major over the upper triangle:
+ *     p(i, j) = i*N - i*(i-1)/2 + (j - i),   0 <= i <= j < N.
+ *
+ * Accumulation is exact in int32. One accumulated sample adds at most 128
+ * in magnitude to an entry (|Re| <= 2*8*8), so a handle refuses to
+ * accumulate more than CORR_MAX_SAMPLES samples between resets.
+ *
+ * Threading and ordering: every call that takes a stream is asynchronous on
+ * that stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream). The caller keeps input and output buffers alive until the work
+ * on the stream has finished. A handle may be used from one host thread at
+ * a time. Consecutive calls on one handle made on different streams are
+ * ordered by an event the handle records after each call.
+ *
+ * Errors: functions return CORR_OK or a negative code and set a
+ * thread-local message (corr_last_error). CUDA failures are sticky on the
+ * handle (corr_status). Kernels never trap; a device-side fault report
+ * (a bounded wait that ran out) is read back by corr_status.
+ */
+#ifndef XENGINE_H
+#define XENGINE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct corr_handle corr_handle_t;
+
+enum {
+  CORR_OK = 0,
+  CORR_EINVAL = -1,    /* bad argument: NULL handle, size out of range, bad pointer kind */
+  CORR_ENOMEM = -2,    /* device or host allocation failed */
+  CORR_ECUDA = -3,     /* a CUDA call failed; sticky on the handle */
+  CORR_EOVERFLOW = -4, /* accumulating would exceed CORR_MAX_SAMPLES since the last reset */
+  CORR_ETIMEOUT = -5,  /* a bounded wait ran out (host deadline or device wait) */
+  CORR_EBUSY = -6      /* the handle still has work in flight where the call needs it idle */
+};
+
+#define CORR_MAX_N 16384
+/* floor((2^31 - 1) / 128): samples an int32 accumulator can take without overflow */
+#define CORR_MAX_SAMPLES 16777215
+
+/*
+ * corr_create -- make a handle for frames of N elements, F bands and T time
+ * samples (1 <= N <= CORR_MAX_N, F >= 1, T >= 1, F*B(N)*2 int32 accumulators
+ * addressable). The handle allocates its own device accumulators on the
+ * current CUDA device and starts in the reset (all-zero) state.
+ * Returns NULL on error; corr_last_error() says why.
+ */
+corr_handle_t* corr_create(int32_t N, int32_t F, int32_t T);
+
+/*
+ * corr_create_ex -- as corr_create, but the accumulators live in a caller-
+ * owned device buffer acc_dev of F*N(N+1)/2*2 int32 (e.g. a torch tensor),
+ * 16-byte aligned. The caller keeps it alive until corr_destroy. Its
+ * contents on entry are ignored: the handle starts in the reset state.
+ */
+corr_handle_t* corr_create_ex(int32_t N, int32_t F, int32_t T, int32_t* acc_dev);
+
+/*
+ * corr_accumulate -- add one frame to the handle's accumulators
+ * (Sec. III: results are added to the previous results).
+ * packed_dev: device pointer to uint8 x[T][F][N] (layout above). Any
+ * alignment and any N are accepted; inputs whose rows are not 16-byte
+ * aligned are first copied into an aligned staging buffer on the device.
+ * Asynchronous on `stream`. Returns CORR_EOVERFLOW (and launches nothing)
+ * if the samples since the last reset would exceed CORR_MAX_SAMPLES.
+ */
+int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream);
+
+/*
+ * corr_accumulate_host -- as corr_accumulate with packed_host in host memory
+ * (pinned memory gives full copy speed; pageable memory works). The frame
+ * is copied to the device in time-chunks, each chunk correlated while the
+ * next one is copied. The host buffer must stay unchanged until the stream
+ * has passed this call.
+ */
+int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* stream);
+
+/*
+ * corr_readout -- copy the packed visibilities int32 V[F][B][2] to vis_dev
+ * (device memory, or host memory for corr_readout_host); with reset != 0
+ * the accumulators then return to the all-zero state (Sec. II.A: a new
+ * integration starts). Asynchronous on `stream`.
+ */
+int corr_readout(corr_handle_t* h, int32_t* vis_dev, int reset, void* stream);
+int corr_readout_host(corr_handle_t* h, int32_t* vis_host, int reset, void* stream);
+
+/* corr_reset -- return the accumulators to the all-zero state without a readout. */
+int corr_reset(corr_handle_t* h, void* stream);
+
+/*
+ * corr_accumulate_batch -- one launch for n frames of possibly different
+ * N, F, T: frame k (packed device bytes inputs[k]) is added to handle hs[k].
+ * The frames' tiles share one persistent work list (Sec. II.C: tiles are
+ * independent; Sec. IV: bands are independent). Handles must be distinct.
+ */
+int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream);
+
+/* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit). */
+int corr_synchronize(corr_handle_t* h, int64_t timeout_ms);
+
+/* corr_status -- CORR_OK or the handle's sticky error (CUDA failure or device fault report). */
+int corr_status(corr_handle_t* h);
+
+/* corr_samples -- samples accumulated since the last reset. */
+int64_t corr_samples(const corr_handle_t* h);
+
+/* corr_dims -- N, F, T of the handle (any pointer may be NULL). */
+int corr_dims(const corr_handle_t* h, int32_t* N, int32_t* F, int32_t* T);
+
+/* corr_last_error -- message for the calling thread's last failed call ("" if none). */
+const char* corr_last_error(void);
+
+/* corr_destroy -- wait for the handle's work, free what it owns. NULL is a no-op. */
+void corr_destroy(corr_handle_t* h);
+
+/*
+ * corr_plan_tiles -- host-only scheduler query (no CUDA calls): the number
+ * of tiles covering the upper triangle of an N x N matrix with square tiles
+ * of `tile` elements, nb(nb+1)/2 with nb = ceil(N / tile) (Sec. II.C,
+ * Fig. 1). If bi_out/bj_out are non-NULL they receive the tile coordinates
+ * in launch order (block rows bi <= block columns bj); cap bounds the
+ * entries written. Returns the count, or CORR_EINVAL.
+ */
+int64_t corr_plan_tiles(int32_t N, int32_t tile, int32_t* bi_out, int32_t* bj_out, int64_t cap);
+
+/*
+ * corr_effective_ops -- Eq. 2 per band and time step, times F*T:
+ * 4*N*(N+1)*F*T, the "effective operations" of one frame.
+ */
+double corr_effective_ops(int32_t N, int32_t F, int32_t T);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XENGINE_H */

@@ -1,0 +1,78 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built extension")
+    config.addinivalue_line("markers", "slow: full-size workloads (seconds to minutes)")
+
+
+def pytest_collection_modifyitems(config, items):
+    try:
+        import torch
+        have_gpu = torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        have_gpu = False
+    if have_gpu:
+        return
+    skip = pytest.mark.skip(reason="no CUDA device on this machine")
+    for item in items:
+        if "gpu" in item.keywords:
+            item.add_marker(skip)
+
+
+def read_hand_cases():
+    """Parse tests/golden/hand_cases.txt -> list of (name, N, F, T, bytes[T][F][N], {(f,i,j): (re, im)})."""
+    import numpy as np
+    cases, cur = [], None
+    with open(os.path.join(GOLDEN, "hand_cases.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "case":
+                cur = {"name": tok[1], "dims": None, "rows": [], "V": {}}
+            elif tok[0] == "x":
+                cur["rows"].append([int(b, 16) for b in tok[1:]])
+            elif tok[0] == "V":
+                f, i, j, re, im = map(int, tok[1:])
+                cur["V"][(f, i, j)] = (re, im)
+            elif tok[0] == "end":
+                N, F, T = cur["dims"]
+                x = np.array(cur["rows"], dtype=np.uint8).reshape(T, F, N)
+                cases.append((cur["name"], N, F, T, x, cur["V"]))
+                cur = None
+            else:
+                cur["dims"] = tuple(map(int, tok))
+    return cases
+
+
+def read_decode_cases():
+    out = []
+    with open(os.path.join(GOLDEN, "decode_cases.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                b, re, im = line.split()
+                out.append((int(b, 16), int(re), int(im)))
+    return out
+
+
+def read_paper_numbers():
+    vals = {}
+    with open(os.path.join(GOLDEN, "paper_numbers.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()[:2]
+                vals[k] = float(v)
+    return vals
