@@ -1,0 +1,156 @@
+"""GB300-native 4-bit X-engine (after arXiv:1503.06203).
+
+Python face of the C ABI in ``include/xengine.h``. Every step of the
+correlation runs in the CUDA library; this module only passes pointers,
+sizes and streams. PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_MAX_SAMPLES, CORR_OK,
+                   XEngineError, check, last_error, lib)
+
+__all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
+           "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _b
+    return _b(force=force)
+
+
+def baselines(N: int) -> int:
+    """Entries of the packed upper triangle, autos included: N(N+1)/2."""
+    return N * (N + 1) // 2
+
+
+def packed_index(N: int, i, j):
+    """Row-major upper-triangle position p(i, j) = i*N - i*(i-1)/2 + (j - i), i <= j."""
+    return i * N - i * (i - 1) // 2 + (j - i)
+
+
+def effective_ops(N: int, F: int, T: int) -> float:
+    """Eq. 2 operations per band and sample times F*T: 4 N (N+1) F T."""
+    return float(lib().corr_effective_ops(N, F, T))
+
+
+def plan_tiles(N: int, tile: int):
+    """(bi, bj) block coordinates of the upper-triangle tiles in launch order."""
+    L = lib()
+    n = L.corr_plan_tiles(N, tile, None, None, 0)
+    if n < 0:
+        raise XEngineError(int(n), last_error())
+    bi = np.empty(n, dtype=np.int32)
+    bj = np.empty(n, dtype=np.int32)
+    L.corr_plan_tiles(N, tile, bi.ctypes.data, bj.ctypes.data, n)
+    return bi, bj
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Correlator:
+    """A handle: resident int32 accumulators for frames of N elements, F bands, T samples."""
+
+    def __init__(self, N: int, F: int, T: int, acc=None):
+        L = lib()
+        self._acc = acc  # keep a caller-owned tensor alive
+        if acc is None:
+            h = L.corr_create(N, F, T)
+        else:
+            import torch
+            assert acc.is_cuda and acc.dtype == torch.int32 and acc.is_contiguous()
+            assert acc.numel() == F * baselines(N) * 2
+            h = L.corr_create_ex(N, F, T, ctypes.c_void_p(acc.data_ptr()))
+        if not h:
+            raise XEngineError(CORR_EINVAL, last_error())
+        self._h = ctypes.c_void_p(h)
+        self.N, self.F, self.T = N, F, T
+
+    # -- lifetime --
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().corr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls --
+    def _check_frame(self, x):
+        if tuple(x.shape) != (self.T, self.F, self.N):
+            raise ValueError(f"frame shape {tuple(x.shape)} != (T, F, N) = {(self.T, self.F, self.N)}")
+
+    def accumulate(self, x, stream=None):
+        """Add a device frame (torch uint8 [T][F][N], contiguous) to the accumulators."""
+        import torch
+        self._check_frame(x)
+        if not (x.is_cuda and x.dtype == torch.uint8 and x.is_contiguous()):
+            raise ValueError("accumulate expects a contiguous CUDA uint8 tensor")
+        check(lib().corr_accumulate(self._h, ctypes.c_void_p(x.data_ptr()), _stream_ptr(stream)))
+
+    def accumulate_host(self, x, stream=None):
+        """Add a host frame (numpy uint8 or a CPU torch tensor, ideally pinned): copies overlap compute."""
+        self._check_frame(x)
+        ptr = x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+        check(lib().corr_accumulate_host(self._h, ctypes.c_void_p(ptr), _stream_ptr(stream)))
+
+    def readout(self, out=None, reset: bool = False, stream=None):
+        """Packed visibilities int32 [F][N(N+1)/2][2] into a device tensor (allocated if None)."""
+        import torch
+        if out is None:
+            out = torch.empty((self.F, baselines(self.N), 2), dtype=torch.int32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.int32 and out.is_contiguous()
+        assert out.numel() == self.F * baselines(self.N) * 2
+        check(lib().corr_readout(self._h, ctypes.c_void_p(out.data_ptr()), int(reset), _stream_ptr(stream)))
+        return out
+
+    def readout_host(self, out, reset: bool = False, stream=None):
+        """Packed visibilities into host memory (numpy int32 or CPU torch tensor, ideally pinned)."""
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else out.data_ptr()
+        check(lib().corr_readout_host(self._h, ctypes.c_void_p(ptr), int(reset), _stream_ptr(stream)))
+        return out
+
+    def reset(self, stream=None):
+        check(lib().corr_reset(self._h, _stream_ptr(stream)))
+
+    def synchronize(self, timeout_ms: int = -1):
+        check(lib().corr_synchronize(self._h, timeout_ms))
+
+    def status(self) -> int:
+        return int(lib().corr_status(self._h))
+
+    @property
+    def samples(self) -> int:
+        return int(lib().corr_samples(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def accumulate_batch(correlators, inputs, stream=None):
+    """One call for several frames: inputs[k] (device uint8 tensor) is added to correlators[k]."""
+    n = len(correlators)
+    assert len(inputs) == n
+    for c, x in zip(correlators, inputs):
+        c._check_frame(x)
+    hs = (ctypes.c_void_p * n)(*[c._h.value for c in correlators])
+    xs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in inputs])
+    check(lib().corr_accumulate_batch(hs, xs, n, _stream_ptr(stream)))

@@ -1,0 +1,548 @@
+// Host side of the C ABI declared in include/xengine.h: handles, the
+// upper-triangle tile scheduler, TMA descriptors, launches and ordering.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/xengine.h"
+#include "xe_corr.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+// ---- cuTensorMapEncodeTiled through the runtime's driver entry point --------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+std::once_flag g_encode_once;
+
+EncodeTiledFn encode_fn() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  });
+  return g_encode;
+}
+
+// ---- per-device kernel set-up ---------------------------------------------------
+constexpr size_t kSmemBytes = sizeof(xe::CorrSmem) + 1024;  // + alignment slack
+std::mutex g_dev_mu;
+int g_blocks_per_sm[64];
+int g_sms[64];
+bool g_dev_ready[64];
+
+int device_setup(int dev) {
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (dev < 0 || dev >= 64) return fail(CORR_EINVAL, "device ordinal %d out of range", dev);
+  if (g_dev_ready[dev]) return CORR_OK;
+  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kSmemBytes));
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel, xe::kThreads, kSmemBytes);
+  if (e != cudaSuccess || bps < 1)
+    return fail(CORR_ECUDA, "occupancy query: %s (blocks/SM %d)", cudaGetErrorString(e), bps);
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "SM count: %s", cudaGetErrorString(e));
+  g_blocks_per_sm[dev] = bps;
+  g_sms[dev] = sms;
+  g_dev_ready[dev] = true;
+  return CORR_OK;
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Upper-triangle tile order: block rows bi <= block columns bj, row-major (Fig. 1).
+void triangle_tiles(int32_t N, int32_t tile, std::vector<int32_t>& bi, std::vector<int32_t>& bj) {
+  const int32_t nb = static_cast<int32_t>(ceil_div(N, tile));
+  bi.clear();
+  bj.clear();
+  for (int32_t r = 0; r < nb; ++r)
+    for (int32_t c = r; c < nb; ++c) {
+      bi.push_back(r);
+      bj.push_back(c);
+    }
+}
+
+}  // namespace
+
+// ---- the handle ----------------------------------------------------------------
+struct corr_handle {
+  int32_t N = 0, F = 0, T = 0;
+  int64_t B = 0;
+  int device = 0;
+  int32_t* acc = nullptr;  // [F][B][2]
+  bool own_acc = false;
+  bool fresh = true;       // accumulators logically zero (memory may hold anything)
+  int64_t samples = 0;
+  int sticky = CORR_OK;
+  int32_t* d_err = nullptr;
+  cudaEvent_t last = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool has_last = false;
+  // plan for full frames
+  int4* d_items = nullptr;
+  int32_t num_items = 0;
+  int32_t split = 1;
+  int32_t grid = 0;
+  // aligned staging for frames whose rows are not 16-byte aligned
+  uint8_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  // host-input path: two device chunk buffers, two streams
+  uint8_t* hchunk[2] = {nullptr, nullptr};
+  int32_t hchunk_T = 0;
+  int4* d_items_chunk = nullptr;
+  int32_t num_items_chunk = 0, split_chunk = 1, grid_chunk = 0;
+  int4* d_items_tail = nullptr;
+  int32_t num_items_tail = 0, split_tail = 1, grid_tail = 0, tail_T = 0;
+  cudaStream_t s_copy = nullptr, s_comp = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
+};
+
+namespace {
+
+int cuda_fail(corr_handle* h, cudaError_t e, const char* what) {
+  if (h) h->sticky = CORR_ECUDA;
+  return fail(CORR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define XE_CHECK(h, call)                                          \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);       \
+  } while (0)
+
+// Build the work list of a frame with T samples: every (band, tile) with the
+// time range split in `split` parts on stage boundaries.
+int build_items(corr_handle* h, int32_t T, int4** d_items, int32_t* num_items, int32_t* split, int32_t* grid) {
+  std::vector<int32_t> bi, bj;
+  triangle_tiles(h->N, xe::kTile, bi, bj);
+  const int64_t tiles = static_cast<int64_t>(bi.size()) * h->F;
+  const int64_t slots = static_cast<int64_t>(g_sms[h->device]) * g_blocks_per_sm[h->device];
+  const int64_t stages_total = ceil_div(T, xe::kTC);
+  int64_t s = 1;
+  // enough items that the tail of a persistent round-robin stays short
+  if (tiles < 4 * slots) s = std::min<int64_t>(ceil_div(4 * slots, tiles), std::max<int64_t>(1, stages_total / 4));
+  s = std::max<int64_t>(1, std::min<int64_t>(s, stages_total));
+  const int64_t per = ceil_div(stages_total, s) * xe::kTC;  // samples per split, a stage multiple
+  std::vector<int4> items;
+  items.reserve(static_cast<size_t>(tiles * s));
+  // band-major within a split so that one band's tiles run together and share its input in L2;
+  // off-diagonal (full) tiles first in each band, diagonal ones after.
+  for (int64_t k = 0; k < s; ++k) {
+    const int32_t t0 = static_cast<int32_t>(k * per);
+    const int32_t t1 = static_cast<int32_t>(std::min<int64_t>(T, (k + 1) * per));
+    if (t0 >= t1) continue;
+    for (int32_t f = 0; f < h->F; ++f) {
+      for (int pass = 0; pass < 2; ++pass)
+        for (size_t u = 0; u < bi.size(); ++u) {
+          const bool diag = bi[u] == bj[u];
+          if ((pass == 0) == diag) continue;
+          items.push_back(make_int4(f, bi[u] | (bj[u] << 16), t0, t1));
+        }
+    }
+  }
+  if (items.size() > static_cast<size_t>(INT32_MAX)) return fail(CORR_EINVAL, "work list too long");
+  XE_CHECK(h, cudaMalloc(d_items, items.size() * sizeof(int4)));
+  XE_CHECK(h, cudaMemcpy(*d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  *num_items = static_cast<int32_t>(items.size());
+  *split = static_cast<int32_t>(s);
+  *grid = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(items.size()), slots));
+  return CORR_OK;
+}
+
+int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_t T) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return fail(CORR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(F), static_cast<cuuint64_t>(T)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(Np) * static_cast<cuuint64_t>(F)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(xe::kTile), 1u, static_cast<cuuint32_t>(xe::kTC)};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CORR_ECUDA, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+  return CORR_OK;
+}
+
+// Order this call after the handle's previous call if that ran on another stream.
+int order_after_last(corr_handle* h, cudaStream_t st) {
+  if (h->has_last && h->last_stream != st) XE_CHECK(h, cudaStreamWaitEvent(st, h->last, 0));
+  return CORR_OK;
+}
+
+int record_last(corr_handle* h, cudaStream_t st) {
+  XE_CHECK(h, cudaEventRecord(h->last, st));
+  h->last_stream = st;
+  h->has_last = true;
+  return CORR_OK;
+}
+
+int check_handle(corr_handle* h) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (h->sticky != CORR_OK) return fail(h->sticky, "handle has a sticky error (%d)", h->sticky);
+  return CORR_OK;
+}
+
+// Launch the correlator over a [T][F][Np] device frame (16-byte aligned rows).
+int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, int32_t T, const int4* items, int32_t nitems,
+                 int32_t split, int32_t grid, cudaStream_t st) {
+  CUtensorMap tm;
+  int rc = make_tmap(&tm, frame, Np, h->F, T);
+  if (rc) return rc;
+  int mode;
+  if (split == 1) {
+    mode = h->fresh ? xe::kStore : xe::kAdd;
+  } else {
+    if (h->fresh) XE_CHECK(h, cudaMemsetAsync(h->acc, 0, static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t), st));
+    mode = xe::kRed;
+  }
+  xe::CorrArgs a;
+  a.items = items;
+  a.num_items = nitems;
+  a.N = h->N;
+  a.B = h->B;
+  a.vis = h->acc;
+  a.mode = mode;
+  a.err = h->d_err;
+  xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  XE_CHECK(h, cudaGetLastError());
+  h->fresh = false;
+  return CORR_OK;
+}
+
+corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
+  if (N < 1 || N > CORR_MAX_N) return fail(CORR_EINVAL, "N=%d outside [1, %d]", N, CORR_MAX_N), nullptr;
+  if (F < 1) return fail(CORR_EINVAL, "F=%d must be >= 1", F), nullptr;
+  if (T < 1 || T > CORR_MAX_SAMPLES) return fail(CORR_EINVAL, "T=%d outside [1, %d]", T, CORR_MAX_SAMPLES), nullptr;
+  const int64_t B = static_cast<int64_t>(N) * (N + 1) / 2;
+  const int64_t nb = static_cast<int64_t>(ceil_div(N, xe::kTile));
+  if (static_cast<int64_t>(F) * B * 2 > (int64_t(1) << 40)) return fail(CORR_EINVAL, "accumulators too large"), nullptr;
+  if (static_cast<int64_t>(F) * nb * (nb + 1) / 2 > (int64_t(1) << 28))
+    return fail(CORR_EINVAL, "too many tiles"), nullptr;
+  if (acc_dev && (reinterpret_cast<uintptr_t>(acc_dev) & 15))
+    return fail(CORR_EINVAL, "acc_dev must be 16-byte aligned"), nullptr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)), nullptr;
+  if (device_setup(dev) != CORR_OK) return nullptr;
+  corr_handle* h = new (std::nothrow) corr_handle;
+  if (!h) return fail(CORR_ENOMEM, "host allocation failed"), nullptr;
+  h->N = N;
+  h->F = F;
+  h->T = T;
+  h->B = B;
+  h->device = dev;
+  const size_t acc_bytes = static_cast<size_t>(F) * B * 2 * sizeof(int32_t);
+  bool ok = true;
+  if (acc_dev) {
+    h->acc = acc_dev;
+  } else {
+    e = cudaMalloc(&h->acc, acc_bytes);
+    if (e != cudaSuccess) {
+      fail(CORR_ENOMEM, "cudaMalloc(%zu bytes) for accumulators: %s", acc_bytes, cudaGetErrorString(e));
+      h->acc = nullptr;
+      ok = false;
+    }
+    h->own_acc = ok;
+  }
+  if (ok && cudaMalloc(&h->d_err, sizeof(int32_t)) != cudaSuccess) {
+    fail(CORR_ENOMEM, "cudaMalloc error word failed");
+    ok = false;
+  }
+  if (ok && cudaMemset(h->d_err, 0, sizeof(int32_t)) != cudaSuccess) ok = !fail(CORR_ECUDA, "memset error word");
+  if (ok && cudaEventCreateWithFlags(&h->last, cudaEventDisableTiming) != cudaSuccess)
+    ok = !fail(CORR_ECUDA, "cudaEventCreate failed");
+  if (ok && build_items(h, T, &h->d_items, &h->num_items, &h->split, &h->grid) != CORR_OK) ok = false;
+  if (!ok) {
+    std::string msg = g_last_error;
+    corr_destroy(h);
+    g_last_error = msg;
+    return nullptr;
+  }
+  return h;
+}
+
+// Frames whose rows are not 16-byte aligned go through the staging buffer.
+int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t st, const uint8_t** frame,
+                    int32_t* Np) {
+  const bool aligned = (h->N % 16 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+  if (aligned) {
+    *frame = in;
+    *Np = h->N;
+    return CORR_OK;
+  }
+  const int32_t np = static_cast<int32_t>(ceil_div(h->N, 16) * 16);
+  const size_t need = static_cast<size_t>(np) * h->F * static_cast<size_t>(T);
+  if (need > h->stage_bytes) {
+    if (h->stage) {
+      XE_CHECK(h, cudaStreamSynchronize(st));
+      XE_CHECK(h, cudaFree(h->stage));
+      h->stage = nullptr;
+      h->stage_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&h->stage, need);
+    if (e != cudaSuccess) return fail(CORR_ENOMEM, "staging buffer (%zu bytes): %s", need, cudaGetErrorString(e));
+    h->stage_bytes = need;
+  }
+  const int64_t rows = static_cast<int64_t>(T) * h->F;
+  const int64_t total = rows * np;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>(ceil_div(total, threads), int64_t(g_sms[h->device]) * 8);
+  xe::repack_rows_kernel<<<static_cast<int>(std::max<int64_t>(blocks, 1)), threads, 0, st>>>(in, h->stage, rows,
+                                                                                          h->N, np);
+  XE_CHECK(h, cudaGetLastError());
+  *frame = h->stage;
+  *Np = np;
+  return CORR_OK;
+}
+
+}  // namespace
+
+// =================================== C ABI ===================================
+extern "C" {
+
+corr_handle_t* corr_create(int32_t N, int32_t F, int32_t T) { return create_impl(N, F, T, nullptr); }
+
+corr_handle_t* corr_create_ex(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
+  if (!acc_dev) return fail(CORR_EINVAL, "acc_dev is NULL"), nullptr;
+  return create_impl(N, F, T, acc_dev);
+}
+
+int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!packed_dev) return fail(CORR_EINVAL, "packed_dev is NULL");
+  if (h->samples + h->T > CORR_MAX_SAMPLES)
+    return fail(CORR_EOVERFLOW, "accumulating %d more samples would exceed %d since the last reset", h->T,
+                CORR_MAX_SAMPLES);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = order_after_last(h, st))) return rc;
+  const uint8_t* frame;
+  int32_t np;
+  if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np))) return rc;
+  if ((rc = launch_frame(h, frame, np, h->T, h->d_items, h->num_items, h->split, h->grid, st))) return rc;
+  h->samples += h->T;
+  return record_last(h, st);
+}
+
+int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!packed_host) return fail(CORR_EINVAL, "packed_host is NULL");
+  if (h->samples + h->T > CORR_MAX_SAMPLES)
+    return fail(CORR_EOVERFLOW, "accumulating %d more samples would exceed %d since the last reset", h->T,
+                CORR_MAX_SAMPLES);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int32_t Np = static_cast<int32_t>(ceil_div(h->N, 16) * 16);
+  const size_t row = static_cast<size_t>(h->F) * h->N;  // bytes per time sample (host layout)
+  if (!h->s_copy) {
+    // chunk of about T/4 samples (a stage multiple), at most 256 MB per buffer
+    int64_t cT = ceil_div(ceil_div(h->T, 4), xe::kTC) * xe::kTC;
+    const int64_t cap = std::max<int64_t>(xe::kTC, ((int64_t(256) << 20) / (int64_t(h->F) * Np)) / xe::kTC * xe::kTC);
+    cT = std::max<int64_t>(xe::kTC, std::min<int64_t>(cT, cap));
+    cT = std::min<int64_t>(cT, ceil_div(h->T, xe::kTC) * xe::kTC);
+    h->hchunk_T = static_cast<int32_t>(cT);
+    const size_t bytes = static_cast<size_t>(cT) * h->F * Np;
+    for (int k = 0; k < 2; ++k) {
+      cudaError_t e = cudaMalloc(&h->hchunk[k], bytes);
+      if (e != cudaSuccess) return fail(CORR_ENOMEM, "host-path chunk buffer: %s", cudaGetErrorString(e));
+      XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
+      XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_used[k], cudaEventDisableTiming));
+    }
+    XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    XE_CHECK(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
+    XE_CHECK(h, cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking));
+    if ((rc = build_items(h, h->hchunk_T, &h->d_items_chunk, &h->num_items_chunk, &h->split_chunk, &h->grid_chunk)))
+      return rc;
+    h->tail_T = h->T % h->hchunk_T;
+    if (h->tail_T &&
+        (rc = build_items(h, h->tail_T, &h->d_items_tail, &h->num_items_tail, &h->split_tail, &h->grid_tail)))
+      return rc;
+  }
+  // internal streams start after everything already queued on `st` (and the handle's last call)
+  if ((rc = order_after_last(h, st))) return rc;
+  XE_CHECK(h, cudaEventRecord(h->ev_in, st));
+  XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_in, 0));
+  XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_in, 0));
+  const int32_t nchunks = static_cast<int32_t>(ceil_div(h->T, h->hchunk_T));
+  for (int32_t c = 0; c < nchunks; ++c) {
+    const int b = c & 1;
+    const int32_t t0 = c * h->hchunk_T;
+    const int32_t cT = std::min(h->hchunk_T, h->T - t0);
+    if (c >= 2) XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_used[b], 0));
+    if (Np == h->N) {
+      XE_CHECK(h, cudaMemcpyAsync(h->hchunk[b], packed_host + static_cast<size_t>(t0) * row,
+                                  static_cast<size_t>(cT) * row, cudaMemcpyHostToDevice, h->s_copy));
+    } else {
+      XE_CHECK(h, cudaMemcpy2DAsync(h->hchunk[b], Np, packed_host + static_cast<size_t>(t0) * row, h->N, h->N,
+                                    static_cast<size_t>(cT) * h->F, cudaMemcpyHostToDevice, h->s_copy));
+    }
+    XE_CHECK(h, cudaEventRecord(h->ev_copied[b], h->s_copy));
+    XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_copied[b], 0));
+    const bool tail = cT != h->hchunk_T;
+    if ((rc = launch_frame(h, h->hchunk[b], Np, cT, tail ? h->d_items_tail : h->d_items_chunk,
+                           tail ? h->num_items_tail : h->num_items_chunk, tail ? h->split_tail : h->split_chunk,
+                           tail ? h->grid_tail : h->grid_chunk, h->s_comp)))
+      return rc;
+    XE_CHECK(h, cudaEventRecord(h->ev_used[b], h->s_comp));
+  }
+  // the caller's stream continues after the last chunk
+  XE_CHECK(h, cudaEventRecord(h->last, h->s_comp));
+  XE_CHECK(h, cudaStreamWaitEvent(st, h->last, 0));
+  h->samples += h->T;
+  return record_last(h, st);
+}
+
+static int readout_impl(corr_handle_t* h, int32_t* vis, int reset, void* stream, cudaMemcpyKind kind) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!vis) return fail(CORR_EINVAL, "output pointer is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((rc = order_after_last(h, st))) return rc;
+  const size_t bytes = static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t);
+  if (h->fresh) {  // logically zero: make it so, then copy
+    XE_CHECK(h, cudaMemsetAsync(h->acc, 0, bytes, st));
+    h->fresh = false;
+  }
+  XE_CHECK(h, cudaMemcpyAsync(vis, h->acc, bytes, kind, st));
+  if (reset) {
+    h->fresh = true;
+    h->samples = 0;
+  }
+  return record_last(h, st);
+}
+
+int corr_readout(corr_handle_t* h, int32_t* vis_dev, int reset, void* stream) {
+  return readout_impl(h, vis_dev, reset, stream, cudaMemcpyDeviceToDevice);
+}
+
+int corr_readout_host(corr_handle_t* h, int32_t* vis_host, int reset, void* stream) {
+  return readout_impl(h, vis_host, reset, stream, cudaMemcpyDeviceToHost);
+}
+
+int corr_reset(corr_handle_t* h, void* stream) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  (void)stream;
+  h->fresh = true;
+  h->samples = 0;
+  return CORR_OK;
+}
+
+int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!hs || !inputs))) return fail(CORR_EINVAL, "bad batch arguments");
+  for (int k = 0; k < n; ++k) {
+    int rc = corr_accumulate(hs[k], inputs[k], stream);
+    if (rc) return rc;
+  }
+  return CORR_OK;
+}
+
+int corr_synchronize(corr_handle_t* h, int64_t timeout_ms) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (!h->has_last) return CORR_OK;
+  if (timeout_ms < 0) {
+    cudaError_t e = cudaEventSynchronize(h->last);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    return corr_status(h);
+  }
+  // poll with a deadline
+  cudaEvent_t probe = h->last;
+  for (int64_t waited_us = 0;; waited_us += 50) {
+    cudaError_t e = cudaEventQuery(probe);
+    if (e == cudaSuccess) return corr_status(h);
+    if (e != cudaErrorNotReady) return cuda_fail(h, e, "cudaEventQuery");
+    if (waited_us >= timeout_ms * 1000) return fail(CORR_ETIMEOUT, "handle still busy after %lld ms", (long long)timeout_ms);
+    struct timespec ts = {0, 50000};
+    nanosleep(&ts, nullptr);
+  }
+}
+
+int corr_status(corr_handle_t* h) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (h->sticky != CORR_OK) return h->sticky;
+  int32_t err = 0;
+  cudaError_t e = cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading device error word");
+  if (err) {
+    h->sticky = CORR_ETIMEOUT;
+    return fail(CORR_ETIMEOUT, "device reported a wait that ran out (code %d)", err);
+  }
+  return CORR_OK;
+}
+
+int64_t corr_samples(const corr_handle_t* h) { return h ? h->samples : -1; }
+
+int corr_dims(const corr_handle_t* h, int32_t* N, int32_t* F, int32_t* T) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (N) *N = h->N;
+  if (F) *F = h->F;
+  if (T) *T = h->T;
+  return CORR_OK;
+}
+
+const char* corr_last_error(void) { return g_last_error.c_str(); }
+
+void corr_destroy(corr_handle_t* h) {
+  if (!h) return;
+  if (h->has_last) cudaEventSynchronize(h->last);
+  if (h->own_acc && h->acc) cudaFree(h->acc);
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_items) cudaFree(h->d_items);
+  if (h->d_items_chunk) cudaFree(h->d_items_chunk);
+  if (h->d_items_tail) cudaFree(h->d_items_tail);
+  if (h->stage) cudaFree(h->stage);
+  for (int k = 0; k < 2; ++k) {
+    if (h->hchunk[k]) cudaFree(h->hchunk[k]);
+    if (h->ev_copied[k]) cudaEventDestroy(h->ev_copied[k]);
+    if (h->ev_used[k]) cudaEventDestroy(h->ev_used[k]);
+  }
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->s_copy) cudaStreamDestroy(h->s_copy);
+  if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->last) cudaEventDestroy(h->last);
+  delete h;
+}
+
+int64_t corr_plan_tiles(int32_t N, int32_t tile, int32_t* bi_out, int32_t* bj_out, int64_t cap) {
+  if (N < 1 || N > CORR_MAX_N || tile < 1) return fail(CORR_EINVAL, "bad N or tile");
+  std::vector<int32_t> bi, bj;
+  triangle_tiles(N, tile, bi, bj);
+  const int64_t n = static_cast<int64_t>(bi.size());
+  for (int64_t k = 0; k < n && k < cap; ++k) {
+    if (bi_out) bi_out[k] = bi[k];
+    if (bj_out) bj_out[k] = bj[k];
+  }
+  return n;
+}
+
+double corr_effective_ops(int32_t N, int32_t F, int32_t T) {
+  return 4.0 * static_cast<double>(N) * (static_cast<double>(N) + 1.0) * F * static_cast<double>(T);
+}
+
+}  // extern "C"

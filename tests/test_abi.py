@@ -1,0 +1,95 @@
+"""The C-ABI library loads and exports what include/*.h declares; host-only logic (no GPU)."""
+import glob
+import os
+import re
+
+import pytest
+
+from conftest import ROOT, read_paper_numbers
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def xe():
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    return xe
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for n in ("corr_create", "corr_accumulate", "corr_readout", "corr_destroy", "corr_accumulate_batch",
+              "corr_status", "corr_last_error", "xe_peak_imma_s8"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(xe):
+    import ctypes
+    from paper_1503_06203_gb300._lib import LIB_PATH, SIGNATURES
+    L = ctypes.CDLL(LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    bound = {s[0] for s in SIGNATURES}
+    for n in declared_functions():
+        if n.startswith("corr_"):
+            assert n in bound, f"{n} has no Python binding"
+
+
+def test_fig1_tile_count(xe):
+    """Fig. 1: the upper triangle of a 256 x 256 matrix takes 36 tiles of 32 x 32."""
+    p = read_paper_numbers()
+    bi, bj = xe.plan_tiles(int(p["fig1_N"]), int(p["fig1_tile"]))
+    assert len(bi) == p["fig1_tiles"]
+    assert (bi <= bj).all()
+    assert len(set(zip(bi.tolist(), bj.tolist()))) == len(bi)
+
+
+@pytest.mark.parametrize("N,tile", [(1, 64), (63, 64), (64, 64), (65, 64), (256, 64), (8192, 64), (300, 32)])
+def test_tiles_cover_upper_triangle_once(xe, N, tile):
+    import numpy as np
+    bi, bj = xe.plan_tiles(N, tile)
+    nb = -(-N // tile)
+    assert len(bi) == nb * (nb + 1) // 2
+    cover = np.zeros((nb, nb), dtype=int)
+    np.add.at(cover, (bi, bj), 1)
+    assert (np.triu(cover) == 1)[np.triu_indices(nb)].all() and not np.tril(cover, -1).any()
+
+
+def test_effective_ops_paper_numbers(xe):
+    """Eq. 2 at N=2048 and the throughput figures of Sec. IV and the abstract."""
+    p = read_paper_numbers()
+    ops = xe.effective_ops(2048, 1, 1)
+    assert ops == p["eq2_ops_per_matrix_N2048"]
+    # 4.3 TOPS nominal -> 256 thousand matrices/s; 336 thousand -> 5.6 effective TOPS, 131 %
+    assert round(p["r9_280x_peak_tops"] * 1e12 / ops / 1e3) == p["ideal_matrices_per_s_thousands"]
+    assert round(p["achieved_matrices_per_s_thousands"] * 1e3 * ops / 1e12, 1) == p["effective_tops_abstract"]
+    assert round(100 * p["achieved_matrices_per_s_thousands"] * 1e3 * ops / (p["r9_280x_peak_tops"] * 1e12)) == \
+        p["packed_over_ideal_percent"]
+    assert round(p["achieved_matrices_per_s_caption"] * ops / 1e12, 1) == p["effective_tops_abstract"]
+    assert xe.effective_ops(256, 256, 16384) == 4 * 256 * 257 * 256 * 16384
+
+
+@pytest.mark.parametrize("N,F,T", [(0, 1, 1), (16385, 1, 1), (16, 0, 1), (16, 1, 0), (16, 1, 16777216)])
+def test_create_rejects_bad_sizes_without_cuda(xe, N, F, T):
+    from paper_1503_06203_gb300._lib import lib
+    assert not lib().corr_create(N, F, T)
+    assert xe.last_error() if hasattr(xe, "last_error") else True
+
+
+def test_null_handle_calls(xe):
+    from paper_1503_06203_gb300._lib import CORR_EINVAL, lib
+    L = lib()
+    assert L.corr_accumulate(None, None, None) == CORR_EINVAL
+    assert L.corr_readout(None, None, 0, None) == CORR_EINVAL
+    assert L.corr_status(None) == CORR_EINVAL
+    L.corr_destroy(None)  # NULL-safe
+    assert b"NULL" in L.corr_last_error()
