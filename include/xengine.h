@@ -129,6 +129,9 @@ int corr_status(corr_handle_t* h);
 /* corr_samples -- samples accumulated since the last reset. */
 int64_t corr_samples(const corr_handle_t* h);
 
+/* corr_kernel_launches -- kernels this handle has launched so far (the library's own kernels only). */
+int64_t corr_kernel_launches(const corr_handle_t* h);
+
 /* corr_dims -- N, F, T of the handle (any pointer may be NULL). */
 int corr_dims(const corr_handle_t* h, int32_t* N, int32_t* F, int32_t* T);
 

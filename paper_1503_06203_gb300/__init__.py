@@ -141,6 +141,10 @@ class Correlator:
         return int(lib().corr_samples(self._h))
 
     @property
+    def kernel_launches(self) -> int:
+        return int(lib().corr_kernel_launches(self._h))
+
+    @property
     def handle(self):
         return self._h
 

@@ -31,11 +31,16 @@ SIGNATURES = [
     ("corr_synchronize", _int, [_vp, _i64]),
     ("corr_status", _int, [_vp]),
     ("corr_samples", _i64, [_vp]),
+    ("corr_kernel_launches", _i64, [_vp]),
     ("corr_dims", _int, [_vp, _vp, _vp, _vp]),
     ("corr_last_error", ctypes.c_char_p, []),
     ("corr_destroy", None, [_vp]),
     ("corr_plan_tiles", _i64, [_i32, _i32, _vp, _vp, _i64]),
     ("corr_effective_ops", ctypes.c_double, [_i32, _i32, _i32]),
+    # microbenchmarks (include/xengine_peaks.h)
+    ("xe_peak_imma_s8", ctypes.c_double, [_int, _vp]),
+    ("xe_peak_dp4a", ctypes.c_double, [_int, _vp]),
+    ("xe_peak_imma_dp4a", ctypes.c_double, [_int, _int, _vp, _vp, _vp]),
 ]
 
 _lib = None

@@ -99,6 +99,7 @@ struct corr_handle {
   bool own_acc = false;
   bool fresh = true;       // accumulators logically zero (memory may hold anything)
   int64_t samples = 0;
+  int64_t launches = 0;    // kernels launched by this handle
   int sticky = CORR_OK;
   int32_t* d_err = nullptr;
   cudaEvent_t last = nullptr;
@@ -231,6 +232,7 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, int32_t T, co
   a.err = h->d_err;
   xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
+  ++h->launches;
   h->fresh = false;
   return CORR_OK;
 }
@@ -316,6 +318,7 @@ int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t s
   xe::repack_rows_kernel<<<static_cast<int>(std::max<int64_t>(blocks, 1)), threads, 0, st>>>(in, h->stage, rows,
                                                                                           h->N, np);
   XE_CHECK(h, cudaGetLastError());
+  ++h->launches;
   *frame = h->stage;
   *Np = np;
   return CORR_OK;
@@ -497,6 +500,8 @@ int corr_status(corr_handle_t* h) {
 }
 
 int64_t corr_samples(const corr_handle_t* h) { return h ? h->samples : -1; }
+
+int64_t corr_kernel_launches(const corr_handle_t* h) { return h ? h->launches : -1; }
 
 int corr_dims(const corr_handle_t* h, int32_t* N, int32_t* F, int32_t* T) {
   if (!h) return fail(CORR_EINVAL, "NULL handle");
