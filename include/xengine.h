@@ -152,6 +152,20 @@ void corr_destroy(corr_handle_t* h);
 int64_t corr_plan_tiles(int32_t N, int32_t tile, int32_t* bi_out, int32_t* bj_out, int64_t cap);
 
 /*
+ * corr_plan_schedule -- host-only scheduler query (no CUDA calls): the work
+ * items the library launches for a frame of N, F, T on `ctas` resident CTAs.
+ * Tiles are 64 x 64, band-major, row-major over each band's upper triangle
+ * (Sec. II.C); time is cut into 64-sample chunks, and into `split` equal
+ * ranges of chunks when whole tiles would leave the CTAs unbalanced. Item k
+ * is {band f, bi | bj << 16, first chunk, end chunk} (4 int32 each in
+ * items_out, at most items_cap items); CTA c runs items c, c + grid, ...
+ * *grid_out (if non-NULL) receives the grid size. Returns the item count, or
+ * CORR_EINVAL.
+ */
+int64_t corr_plan_schedule(int32_t N, int32_t F, int32_t T, int32_t ctas, int32_t* items_out, int64_t items_cap,
+                           int32_t* grid_out);
+
+/*
  * corr_effective_ops -- Eq. 2 per band and time step, times F*T:
  * 4*N*(N+1)*F*T, the "effective operations" of one frame.
  */

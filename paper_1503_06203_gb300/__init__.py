@@ -14,11 +14,11 @@ from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_
                    XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _b
+    from .builder import build as _b
     return _b(force=force)
 
 
@@ -47,6 +47,18 @@ def plan_tiles(N: int, tile: int):
     bj = np.empty(n, dtype=np.int32)
     L.corr_plan_tiles(N, tile, bi.ctypes.data, bj.ctypes.data, n)
     return bi, bj
+
+
+def plan_schedule(N: int, F: int, T: int, ctas: int):
+    """(items int32 [K][4] = {f, bi | bj << 16, c0, c1}, grid) the library launches; CTA c runs items c, c+grid, ..."""
+    L = lib()
+    n = L.corr_plan_schedule(N, F, T, ctas, None, 0, None)
+    if n < 0:
+        raise XEngineError(int(n), last_error())
+    items = np.empty((n, 4), dtype=np.int32)
+    grid = ctypes.c_int32()
+    L.corr_plan_schedule(N, F, T, ctas, items.ctypes.data, n, ctypes.byref(grid))
+    return items, grid.value
 
 
 def _stream_ptr(stream):

@@ -36,6 +36,7 @@ SIGNATURES = [
     ("corr_last_error", ctypes.c_char_p, []),
     ("corr_destroy", None, [_vp]),
     ("corr_plan_tiles", _i64, [_i32, _i32, _vp, _vp, _i64]),
+    ("corr_plan_schedule", _i64, [_i32, _i32, _i32, _i32, _vp, _i64, _vp]),
     ("corr_effective_ops", ctypes.c_double, [_i32, _i32, _i32]),
     # microbenchmarks (include/xengine_peaks.h)
     ("xe_peak_imma_s8", ctypes.c_double, [_int, _vp]),
@@ -58,7 +59,7 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(
-                f"the CUDA library {LIB_PATH} is not built; run `python -m paper_1503_06203_gb300.build` "
+                f"the CUDA library {LIB_PATH} is not built; run `python -m paper_1503_06203_gb300.builder` "
                 "(there is no CPU fallback)")
         L = ctypes.CDLL(LIB_PATH)
         for name, res, args in SIGNATURES:

@@ -1,16 +1,20 @@
-// The correlator kernel: TMA-staged 4-bit input, in-register excess-8
-// unpack, integer tensor-core Hermitian product, packed upper-triangle
-// writer. One CTA computes one 64x64 tile (block row bi <= block column bj)
-// of one band over a time range; tiles below the diagonal are never
-// scheduled (Sec. II.C, Fig. 1 of the paper).
+// The correlator kernel: TMA-staged 4-bit input, excess-8 unpack into
+// K-major int8 planes in shared memory, integer tensor-core Hermitian
+// product in the three-product form, packed upper-triangle writer.
 //
-// Arithmetic (Eq. 1): with each sample's parts interleaved along the
-// reduction axis, k = 2t + {0: re, 1: im},
-//   Re V[i,j] = sum_k A[i,k] * Bre[j,k],  A = Bre = (re, im) per sample
-//   Im V[i,j] = sum_k A[i,k] * Bim[j,k],  Bim = (-im, re) per sample
-// so both are int8 x int8 -> int32 dot products on the tensor cores.
-// Every product is exact; sums are exact in int32 up to the sample cap
-// enforced on the host.
+// A CTA walks a contiguous range of (tile, time-chunk) units of one frame.
+// Tiles are 64x64 blocks (block row bi <= block column bj) of one band;
+// tiles below the diagonal are never scheduled (Sec. II.C, Fig. 1).
+//
+// Arithmetic. Eq. 1 gives Re = sum xr_i xr_j + xi_i xi_j and
+// Im = sum xi_i xr_j - xr_i xi_j. With three real products per pair,
+//   P1 = sum_t xr_i xr_j,   P2 = sum_t xi_i xi_j,
+//   Q  = sum_t (xr_i + xi_i)(xr_j - xi_j)  (= P1 - P2 + Im),
+// Re = P1 + P2 and Im = Q - P1 + P2. Each is an int8 x int8 -> int32 dot
+// product over time (xr, xi in [-8, 7]; xr+xi in [-16, 14]; xr-xi in
+// [-15, 15]), so every product is exact. The int32 sums wrap modulo 2^32;
+// Re and Im themselves stay inside int32 under the host's sample cap, so
+// the wrapped arithmetic gives them exactly.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -19,246 +23,408 @@
 
 namespace xe {
 
-constexpr int kTile = 64;                 // tile edge (elements)
-constexpr int kTC = 64;                   // time samples per pipeline stage
-constexpr int kStages = 4;                // TMA ring depth
-constexpr int kConsumerWarps = 4;         // 2 x 2 warps, 32 x 32 warp tiles
-constexpr int kThreads = (kConsumerWarps + 1) * 32;  // + one TMA producer warp
-constexpr int kBoxBytes = kTile * kTC;    // one operand box per stage
-constexpr uint32_t kSpinLimit = 1u << 24; // bounded mbarrier polls
-
-// Writer modes
-enum : int { kStore = 0, kAdd = 1, kRed = 2 };
+constexpr int kTile = 64;                  // tile edge (elements)
+constexpr int kTC = 64;                    // time samples per chunk (pipeline stage)
+#ifndef XE_STAGES
+#define XE_STAGES 6
+#endif
+#ifndef XE_PLANE_BUFS
+#define XE_PLANE_BUFS 4
+#endif
+constexpr int kStages = XE_STAGES;         // TMA ring depth
+constexpr int kPlaneBufs = XE_PLANE_BUFS;  // unpacked-plane buffers between the unpack and product warps
+constexpr int kMmaWarps = 8;               // product warps: 2 x 4 warps of 32 x 16
+constexpr int kUnpackThreads = 128;        // unpack warpgroup
+constexpr int kThreads = kMmaWarps * 32 + kUnpackThreads;
+constexpr int kBoxBytes = kTile * kTC;     // packed box: [time][element] bytes
+constexpr int kPlaneBytes = kTile * kTC;   // plane: [element][time] int8, swizzled
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded mbarrier polls
 
 // Device fault codes (OR-ed into the error word)
 enum : int { kErrTimeoutFull = 1, kErrTimeoutEmpty = 2 };
 
-// One work item: band f, tile (bi, bj), time range [t0, t1).
-// Packed as int4 {f, bi | bj << 16, t0, t1}.
+// Plane slots. A side (rows i): xr, xi, s = xr + xi. B side (columns j): xr, xi, d = xr - xi.
+enum : int { kPxr = 0, kPxi = 1, kPsd = 2 };
+
 struct CorrArgs {
-  const int4* items;
-  int32_t num_items;
+  const int4* items;    // {band f, bi | bj << 16, first chunk, end chunk}; CTA k takes items k, k+grid, ...
+  int32_t nitems;
+  int32_t nch;          // chunks per tile: ceil(T / kTC)
+  int32_t T;            // samples in the frame
   int32_t N;
-  int64_t B;        // N(N+1)/2
-  int32_t* vis;     // [F][B][2] accumulators
-  int32_t mode;     // kStore / kAdd / kRed
-  int32_t* err;     // device error word
+  int64_t B;            // N(N+1)/2
+  int32_t* vis;         // [F][B][2] accumulators
+  int32_t fresh;        // 1: accumulators hold no integration yet (whole tiles store)
+  int32_t* err;         // device error word
 };
 
 struct __align__(128) CorrSmem {
-  uint8_t box[kStages][2][kBoxBytes];  // [stage][A|B][time][element]
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
-  int abort_flag;
+  uint8_t box[kStages][2][kBoxBytes];          // TMA ring: [stage][A|B][time][element]
+  uint8_t plane[kPlaneBufs][2][3][kPlaneBytes];  // [buffer][A|B][slot][element][time]
+  uint64_t full[kStages];   // box landed (TMA transaction count)
+  uint64_t bempty[kStages]; // box read by all 128 unpack threads
+  uint64_t pfull[kPlaneBufs];   // plane buffer written (128 unpack threads)
+  uint64_t pempty[kPlaneBufs];  // plane buffer read (4 product warps)
 };
 
-// Unpack one packed word (4 time samples of one element, byte u = sample u)
-// into the two mma fragment registers of the (re, im) operand.
-__device__ __forceinline__ void unpack_reim(uint32_t pk, uint32_t& r0, uint32_t& r1, uint32_t& re_out,
-                                            uint32_t& lo_out) {
-  const uint32_t hi = (pk >> 4) & 0x0F0F0F0Fu;
-  const uint32_t lo = pk & 0x0F0F0F0Fu;
-  // nibble - 8 per byte: (v + 0x78) ^ 0x80 has no carry between bytes for v <= 15
-  const uint32_t re = (hi + 0x78787878u) ^ 0x80808080u;
-  const uint32_t im = (lo + 0x78787878u) ^ 0x80808080u;
-  r0 = prmt(re, im, 0x5140);  // re0 im0 re1 im1
-  r1 = prmt(re, im, 0x7362);  // re2 im2 re3 im3
-  re_out = re;
-  lo_out = lo;
+// Swizzle of a plane: 16-byte chunk c of row e sits at chunk c ^ f(e). f
+// makes the ldmatrix reads (8 consecutive rows, one chunk) and the unpack
+// stores below (rows 4eg + slot across a half-warp) free of bank conflicts.
+__device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
+  const int f = ((e >> 1) ^ (e >> 3)) & 3;
+  return static_cast<uint32_t>(e * kTC + ((chunk ^ f) << 4));
 }
 
-// The (-im, re) operand from the pieces unpack_reim produced.
-__device__ __forceinline__ void unpack_negim_re(uint32_t re, uint32_t lo, uint32_t& r0, uint32_t& r1) {
-  // 8 - v per byte: (0x88 - v) ^ 0x80, no borrow between bytes for v <= 15
-  const uint32_t nim = (0x88888888u - lo) ^ 0x80808080u;
-  r0 = prmt(nim, re, 0x5140);  // -im0 re0 -im1 re1
-  r1 = prmt(nim, re, 0x7362);
-}
-
-// Gather element e's bytes at time rows row0 + 4u (u = 0..3) of a [time][element]
-// box into one word; rows at or past `nvalid` read as 0x88 (= 0 + 0i).
+// ---- unpack: packed box [time][element] -> planes [element][time] --------------
+//
+// A thread owns 4 elements (4eg..4eg+3) x 16 samples (16tg..16tg+15) of one
+// block. It loads 16 row words, transposes 4x4 byte blocks with prmt, then
+// turns each 4-sample word into the plane bytes with carry-free byte
+// arithmetic (v = nibble in [0, 15]):
+//   v - 8      = (v + 0x78) ^ 0x80
+//   hi + lo - 16 = (hi + lo + 0x70) ^ 0x80      (xr + xi)
+//   hi - lo    = ((hi | 0x80) - lo) ^ 0x80       (xr - xi)
+// Lanes 16..31 load their rows in the order k ^ 1 and odd element quads
+// store their elements in the order slot ^ 1, so that loads and stores are
+// free of bank conflicts; runtime prmt selectors undo both reorderings.
 template <bool kMasked>
-__device__ __forceinline__ uint32_t gather4(const uint8_t* box, int row0, int e, int nvalid) {
+__device__ __forceinline__ void unpack_unit(const uint8_t* box, uint8_t* pl0, uint8_t* pl1, uint8_t* pl2,
+                                            bool side_b, int eg, int tg, int p, int nvalid) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(box);
-  const int col = e >> 2;
-  const uint32_t bsel = static_cast<uint32_t>(e & 3);
-  uint32_t v[4];
+  uint32_t r[16];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int row = row0 + 4 * u;
-    v[u] = w[row * (kTile / 4) + col];
-    if (kMasked) v[u] = row < nvalid ? v[u] : 0x88888888u;
+  for (int k = 0; k < 16; ++k) {
+    const int t = 16 * tg + (k ^ p);
+    r[k] = w[t * (kTile / 4) + eg];
+    if (kMasked) r[k] = t < nvalid ? r[k] : 0x88888888u;  // 0x88 decodes to 0 + 0i
   }
-  const uint32_t s = bsel | ((bsel + 4) << 4);
-  const uint32_t x01 = prmt(v[0], v[1], s);
-  const uint32_t x23 = prmt(v[2], v[3], s);
-  return prmt(x01, x23, 0x5410);
-}
-
-// One pipeline stage (kTC samples) of a warp's 32x32 piece of the tile.
-// skip: 0 = full warp tile, 1 = on the diagonal (skip sub-tiles strictly
-// below it), 2 = entirely below the diagonal (no work).
-template <bool kMasked>
-__device__ __forceinline__ void stage_mma(const uint8_t* boxA, const uint8_t* boxB, int wm, int wn, int lane,
-                                          int skip, int nvalid, int32_t (&acc_re)[2][4][4],
-                                          int32_t (&acc_im)[2][4][4]) {
-  const int g = lane >> 2, q = lane & 3;
+  const int s = eg & 1;
+  const uint32_t selA = p ? 0x1504u : 0x5140u;  // interleave two rows, bytes 0-1
+  const uint32_t selB = p ? 0x3726u : 0x7362u;  // bytes 2-3
+  const uint32_t lo16 = s ? 0x7632u : 0x5410u;  // slots 0 / 2: element (slot ^ s)
+  const uint32_t hi16 = s ? 0x5410u : 0x7632u;  // slots 1 / 3
+  uint32_t wd[4][4];  // [slot][time quad]
 #pragma unroll
-  for (int ks = 0; ks < kTC / 16; ++ks) {
-    const int row0 = ks * 16 + q;
-    if (kMasked && ks * 16 >= nvalid) break;
-    // A operand: rows wm*32 + mi*16 + g (+8)
-    uint32_t a[2][4];
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t x0 = prmt(r[4 * j], r[4 * j + 1], selA);
+    const uint32_t x1 = prmt(r[4 * j], r[4 * j + 1], selB);
+    const uint32_t y0 = prmt(r[4 * j + 2], r[4 * j + 3], selA);
+    const uint32_t y1 = prmt(r[4 * j + 2], r[4 * j + 3], selB);
+    wd[0][j] = prmt(x0, y0, lo16);
+    wd[1][j] = prmt(x0, y0, hi16);
+    wd[2][j] = prmt(x1, y1, lo16);
+    wd[3][j] = prmt(x1, y1, hi16);
+  }
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
+  for (int k = 0; k < 4; ++k) {
+    const int e = 4 * eg + (k ^ s);
+    uint32_t xr[4], xi[4], sd[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t pk = gather4<kMasked>(boxA, row0, wm * 32 + mi * 16 + g + 8 * h, nvalid);
-        uint32_t r0, r1, re, lo;
-        unpack_reim(pk, r0, r1, re, lo);
-        a[mi][h] = r0;      // a0 / a1: k = 4q..4q+3 of rows g / g+8
-        a[mi][2 + h] = r1;  // a2 / a3: k = 4q+16..4q+19
-      }
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t hi = (wd[k][j] >> 4) & 0x0F0F0F0Fu;
+      const uint32_t lo = wd[k][j] & 0x0F0F0F0Fu;
+      xr[j] = (hi + 0x78787878u) ^ 0x80808080u;
+      xi[j] = (lo + 0x78787878u) ^ 0x80808080u;
+      sd[j] = side_b ? (((hi | 0x80808080u) - lo) ^ 0x80808080u) : ((hi + lo + 0x70707070u) ^ 0x80808080u);
     }
+    const uint32_t off = plane_off(e, tg);
+    if (pl0) *reinterpret_cast<uint4*>(pl0 + off) = make_uint4(xr[0], xr[1], xr[2], xr[3]);
+    if (pl1) *reinterpret_cast<uint4*>(pl1 + off) = make_uint4(xi[0], xi[1], xi[2], xi[3]);
+    *reinterpret_cast<uint4*>(pl2 + off) = make_uint4(sd[0], sd[1], sd[2], sd[3]);
+  }
+}
+
+// ---- product: one 64-sample chunk of a warp's 32 x 16 piece of the tile --------
+// acc[0] = P1, acc[1] = P2, acc[2] = Q, each over the piece's 2 x 2 sub-tiles
+// of 16 x 8. Planes are addressed as shared-memory offsets: A side slot p at
+// a_base + p*kPlaneBytes; B side slots 0-1 at b01_base + p*kPlaneBytes and
+// slot 2 at b2_base (on a diagonal tile the B side's xr, xi planes are the A
+// side's).
+//
+// Sub-tile selection: kSelAll = the whole piece; kSel00 / kSel01 = only the
+// sub-tile (mi = 0, ni = 0 / 1) (used on diagonal tiles, see the kernel).
+enum : int { kSelAll = 0, kSel00 = 1, kSel01 = 2 };
+
+__device__ __forceinline__ constexpr bool sub_on(int sel, int mi, int ni) {
+  return sel == kSelAll || (mi == 0 && ni == sel - 1);
+}
+
+template <int sel>
+__device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pwm, int pwn,
+                                          int lane, int ksteps, int32_t (&acc)[3][2][2][4]) {
+  const int arow = pwm * 32 + (lane & 15);
+  const int brow = pwn * 16 + (lane & 7) + ((lane >> 4) << 3);
+  const int ahalf = lane >> 4, bhalf = (lane >> 3) & 1;
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni) {
-      const uint32_t pk = gather4<kMasked>(boxB, row0, wn * 32 + ni * 8 + g, nvalid);
-      uint32_t b0, b1, re, lo, c0, c1;
-      unpack_reim(pk, b0, b1, re, lo);
-      unpack_negim_re(re, lo, c0, c1);
+  for (int ks = 0; ks < kTC / 32; ++ks) {
+    if (ks >= ksteps) break;
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        if (skip == 1 && mi == 1 && ni < 2) continue;  // sub-tile strictly below the diagonal
-        mma_s8_16832(acc_re[mi][ni], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b0, b1);
-        mma_s8_16832(acc_im[mi][ni], a[mi][0], a[mi][1], a[mi][2], a[mi][3], c0, c1);
-      }
+    for (int pl = 0; pl < 3; ++pl) {
+      const uint32_t pa = a_base + pl * kPlaneBytes;
+      const uint32_t pb = pl < 2 ? b01_base + pl * kPlaneBytes : b2_base;
+      uint32_t a[2][4], b[2][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+        if (sel == kSelAll || mi == 0)
+          ldsm_x4(pa + plane_off(arow + mi * 16, 2 * ks + ahalf), a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+      ldsm_x4(pb + plane_off(brow, 2 * ks + bhalf), b[0][0], b[0][1], b[1][0], b[1][1]);
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni)
+          if (sub_on(sel, mi, ni))
+            mma_s8_16832(acc[pl][mi][ni], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b[ni][0], b[ni][1]);
     }
   }
 }
 
-__device__ __forceinline__ void put_vis(int32_t* p, int32_t re, int32_t im, int mode) {
-  if (mode == kStore) {
-    *reinterpret_cast<int2*>(p) = make_int2(re, im);
-  } else if (mode == kAdd) {
-    int2 v = *reinterpret_cast<int2*>(p);
-    v.x += re;
-    v.y += im;
-    *reinterpret_cast<int2*>(p) = v;
-  } else {
-    atomicAdd(p, re);
-    atomicAdd(p + 1, im);
-  }
-}
-
-// Packed-triangle writer: drop entries with i > j (diagonal tiles) or
-// outside the N x N matrix; entry (i, j) goes to (f*B + p(i,j))*2.
-__device__ __forceinline__ void write_tile(const CorrArgs& a, int f, int i0, int j0, int wm, int wn, int lane,
-                                           const int32_t (&acc_re)[2][4][4], const int32_t (&acc_im)[2][4][4]) {
+// ---- writer: tile piece -> packed upper triangle ---------------------------------
+// mode 0: store (whole tile, fresh integration); 1: add (whole tile onto
+// resident accumulators); 2: atomic add (part of the time range of a tile
+// whose other parts other CTAs add). Entries with i > j, outside the N x N
+// matrix, or in sub-tiles the warp did not compute are dropped; entry (i, j)
+// of band f lives at (f*B + p(i,j))*2, p(i,j) = i*N - i(i-1)/2 + j - i.
+__device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, int j0, int pwm, int pwn, int lane,
+                                            int mode, int sel, int32_t (&acc)[3][2][2][4]) {
+  // fold in place: Re = P1 + P2 into acc[0], Im = Q - P1 + P2 into acc[2] (modulo 2^32;
+  // exact for in-range Re, Im)
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t p1 = static_cast<uint32_t>(acc[0][mi][ni][r]), p2 = static_cast<uint32_t>(acc[1][mi][ni][r]);
+        acc[0][mi][ni][r] = static_cast<int32_t>(p1 + p2);
+        acc[2][mi][ni][r] = static_cast<int32_t>(static_cast<uint32_t>(acc[2][mi][ni][r]) - p1 + p2);
+      }
   const int g = lane >> 2, q = lane & 3;
-  const int64_t N = a.N;
+  const int N = a.N;
   int32_t* base = a.vis + static_cast<int64_t>(f) * a.B * 2;
+  const int jw = j0 + pwn * 16 + 2 * q;
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int64_t i = i0 + wm * 32 + mi * 16 + g + 8 * h;
-      if (i >= N) continue;
-      const int64_t prow = i * N - i * (i - 1) / 2 - i;  // p(i, j) = prow + j
+      const int i = i0 + pwm * 32 + mi * 16 + g + 8 * h;
+      if (i >= N || (sel != kSelAll && mi != 0)) continue;
+      const int64_t ii = i;
+      int32_t* rowp = base + (ii * N - ii * (ii - 1) / 2 - ii) * 2;  // entry (i, j) at rowp + 2j
 #pragma unroll
-      for (int ni = 0; ni < 4; ++ni)
+      for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int64_t j = j0 + wn * 32 + ni * 8 + 2 * q + c;
-          if (j < i || j >= N) continue;
-          put_vis(base + (prow + j) * 2, acc_re[mi][ni][2 * h + c], acc_im[mi][ni][2 * h + c], a.mode);
+          const int j = jw + ni * 8 + c;
+          if (j < i || j >= N || (sel != kSelAll && ni != sel - 1)) continue;
+          const int32_t re = acc[0][mi][ni][2 * h + c], im = acc[2][mi][ni][2 * h + c];
+          int32_t* dst = rowp + 2 * j;
+          if (mode == 0) {
+            *reinterpret_cast<int2*>(dst) = make_int2(re, im);
+          } else if (mode == 1) {
+            int2 v = *reinterpret_cast<int2*>(dst);
+            v.x = static_cast<int32_t>(static_cast<uint32_t>(v.x) + static_cast<uint32_t>(re));
+            v.y = static_cast<int32_t>(static_cast<uint32_t>(v.y) + static_cast<uint32_t>(im));
+            *reinterpret_cast<int2*>(dst) = v;
+          } else {
+            atomicAdd(dst, re);
+            atomicAdd(dst + 1, im);
+          }
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap, CorrArgs args) {
-  extern __shared__ __align__(1024) uint8_t smem_raw[];
-  CorrSmem& sm = *reinterpret_cast<CorrSmem*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+// ---- the kernel ------------------------------------------------------------------
+// Work items are (band, tile, chunk range); CTA k takes items k, k + grid,
+// k + 2 grid, ... in list order. The list is band-major, so the CTAs that run
+// at the same time work on the tiles of one band over the same time chunks
+// and share that band's input in L2.
+//
+// Warp roles. Warps 0-7: tensor-core product and writer, 2 x 4 warps of
+// 32 x 16 (three int32 accumulator sets, 48 registers a thread); two of them
+// share each SM sub-partition. Warps 8-11: unpack; lane 0 of warp 8 also
+// issues the TMA loads. One CTA per SM.
+__device__ __forceinline__ void zero_acc(int32_t (&acc)[3][2][2][4]) {
+#pragma unroll
+  for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[pl][mi][ni][r] = 0;
+}
+
+// Walks (item, chunk) pairs of this CTA in order.
+struct Walk {
+  int item, c, f, bi, bj, c1;
+  const int4* items;
+  int nitems, stride;
+  __device__ __forceinline__ void load() {
+    if (item < nitems) {
+      const int4 w = items[item];
+      f = w.x;
+      bi = w.y & 0xFFFF;
+      bj = w.y >> 16;
+      c = w.z;
+      c1 = w.w;
+    }
+  }
+  __device__ __forceinline__ void start(const int4* it, int n, int first, int step) {
+    items = it;
+    nitems = n;
+    stride = step;
+    item = first;
+    load();
+  }
+  __device__ __forceinline__ bool valid() const { return item < nitems; }
+  __device__ __forceinline__ void next() {
+    if (++c == c1) {
+      item += stride;
+      load();
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                CorrArgs args) {
+  extern __shared__ uint8_t smem_raw[];
+  CorrSmem& sm = *reinterpret_cast<CorrSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                              ~static_cast<uintptr_t>(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sm.full[s], 1);
-      mbar_init(&sm.empty[s], kConsumerWarps);
+      mbar_init(&sm.bempty[s], kUnpackThreads);
     }
-    sm.abort_flag = 0;
+    for (int b = 0; b < kPlaneBufs; ++b) {
+      mbar_init(&sm.pfull[b], kUnpackThreads);
+      mbar_init(&sm.pempty[b], kMmaWarps);
+    }
     fence_barrier_init();
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
-    // ---------------- TMA producer (one thread) ----------------
-    if (lane == 0) {
+  if (warp >= kMmaWarps) {
+    // ================= unpack warps (+ TMA issue) =================
+    const int uw = warp - kMmaWarps;  // 0..3
+    const bool producer = uw == 0 && lane == 0;
+    const int eg = lane & 15, p = lane >> 4, tg = 2 * (uw & 1) + p;
+    Walk ld;  // the TMA issuer walks the same units, kStages ahead
+    ld.start(args.items, args.nitems, blockIdx.x, gridDim.x);
+    uint32_t issued = 0;
+    auto issue = [&](void) {
+      const int s = issued % kStages;
+      const bool diag = ld.bi == ld.bj;
+      mbar_arrive_expect_tx(&sm.full[s], diag ? kBoxBytes : 2 * kBoxBytes);
+      tma_load_3d(sm.box[s][0], &tmap, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
+      if (!diag) tma_load_3d(sm.box[s][1], &tmap, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
+      ++issued;
+      ld.next();
+    };
+    if (producer) {
       tma_prefetch_desc(&tmap);
-      uint32_t it = 0;
-      bool ok = true;
-      for (int item = blockIdx.x; item < args.num_items && ok; item += gridDim.x) {
-        const int4 w = args.items[item];
-        const int f = w.x, bi = w.y & 0xFFFF, bj = w.y >> 16, t0 = w.z, t1 = w.w;
-        const bool diag = bi == bj;
-        for (int t = t0; t < t1; t += kTC, ++it) {
-          const int s = it % kStages;
-          if (it >= kStages && !mbar_wait_bounded(&sm.empty[s], ((it / kStages) - 1) & 1, kSpinLimit)) {
-            atomicOr(args.err, kErrTimeoutEmpty);
-            sm.abort_flag = 1;
-            ok = false;
-            break;
-          }
-          mbar_arrive_expect_tx(&sm.full[s], diag ? kBoxBytes : 2 * kBoxBytes);
-          tma_load_3d(sm.box[s][0], &tmap, &sm.full[s], bi * kTile, f, t);
-          if (!diag) tma_load_3d(sm.box[s][1], &tmap, &sm.full[s], bj * kTile, f, t);
-        }
-      }
-      // Drain: never leave with copies in flight (bounded).
-      const uint32_t first = it > kStages ? it - kStages : 0;
-      for (uint32_t k = first; k < it; ++k) mbar_wait_bounded(&sm.full[k % kStages], (k / kStages) & 1, kSpinLimit);
+      for (int k = 0; k < kStages && ld.valid(); ++k) issue();
     }
-    return;
-  }
-
-  // ---------------- consumers: 4 warps, 2 x 2 warp grid ----------------
-  const int wm = warp >> 1, wn = warp & 1;
-  int32_t acc_re[2][4][4], acc_im[2][4][4];
-  uint32_t it = 0;
-  for (int item = blockIdx.x; item < args.num_items; item += gridDim.x) {
-    const int4 w = args.items[item];
-    const int f = w.x, bi = w.y & 0xFFFF, bj = w.y >> 16, t0 = w.z, t1 = w.w;
-    const bool diag = bi == bj;
-    const int skip = !diag ? 0 : (wm > wn ? 2 : (wm == wn ? 1 : 0));
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc_re[mi][ni][c] = acc_im[mi][ni][c] = 0;
-
+    uint32_t it = 0;
     bool ok = true;
-    for (int t = t0; t < t1; t += kTC, ++it) {
-      const int s = it % kStages;
-      if (!mbar_wait_bounded(&sm.full[s], (it / kStages) & 1, kSpinLimit)) {
+    Walk x;
+    for (x.start(args.items, args.nitems, blockIdx.x, gridDim.x); x.valid(); x.next(), ++it) {
+      const bool diag = x.bi == x.bj;
+      const int s = it % kStages, buf = it % kPlaneBufs;
+      // the plane buffer must be free (its previous chunk's products issued) and the box landed
+      if ((it >= kPlaneBufs && !mbar_wait_bounded(&sm.pempty[buf], ((it / kPlaneBufs) - 1) & 1, kSpinLimit)) ||
+          !mbar_wait_bounded(&sm.full[s], (it / kStages) & 1, kSpinLimit)) {
         if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
         ok = false;
         break;
       }
-      const uint8_t* bA = sm.box[s][0];
-      const uint8_t* bB = diag ? sm.box[s][0] : sm.box[s][1];
-      const int nvalid = t1 - t;
-      if (skip != 2) {
-        if (nvalid >= kTC)
-          stage_mma<false>(bA, bB, wm, wn, lane, skip, kTC, acc_re, acc_im);
-        else
-          stage_mma<true>(bA, bB, wm, wn, lane, skip, nvalid, acc_re, acc_im);
+      const int nvalid = args.T - x.c * kTC;
+      const int blk = diag ? 0 : (uw >> 1);
+      const uint8_t* box = sm.box[s][blk];
+      uint8_t* pl0 = sm.plane[buf][blk][kPxr];
+      uint8_t* pl1 = sm.plane[buf][blk][kPxi];
+      uint8_t* pl2 = sm.plane[buf][blk][kPsd];
+      bool side_b = blk == 1;
+      if (diag && uw >= 2) {  // diagonal tile: warps 6-7 make the B side's xr - xi plane
+        pl0 = pl1 = nullptr;
+        pl2 = sm.plane[buf][1][kPsd];
+        side_b = true;
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&sm.empty[s]);
+      if (nvalid >= kTC)
+        unpack_unit<false>(box, pl0, pl1, pl2, side_b, eg, tg, p, kTC);
+      else
+        unpack_unit<true>(box, pl0, pl1, pl2, side_b, eg, tg, p, nvalid);
+      mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
+      mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
+      if (producer && ld.valid()) {  // refill slot s once every unpack thread is done with it
+        if (!mbar_wait_bounded(&sm.bempty[s], (it / kStages) & 1, kSpinLimit)) {
+          atomicOr(args.err, kErrTimeoutEmpty);
+          ok = false;
+          break;
+        }
+        issue();
+      }
     }
-    if (!ok) return;
-    if (skip != 2) write_tile(args, f, bi * kTile, bj * kTile, wm, wn, lane, acc_re, acc_im);
+    if (producer) {  // never leave with copies in flight (bounded)
+      const uint32_t first = issued > kStages ? issued - kStages : 0;
+      for (uint32_t k = first; k < issued; ++k)
+        mbar_wait_bounded(&sm.full[k % kStages], (k / kStages) & 1, ok ? kSpinLimit : 1024u);
+    }
+    return;
+  }
+
+  // ================= product warps =================
+  const int wm = warp >> 2, wn = warp & 3;
+  int32_t acc[3][2][2][4];
+  zero_acc(acc);
+  uint32_t it = 0;
+  Walk x;
+  for (x.start(args.items, args.nitems, blockIdx.x, gridDim.x); x.valid(); ++it) {
+    const bool diag = x.bi == x.bj;
+    const int buf = it % kPlaneBufs;
+    if (!mbar_wait_bounded(&sm.pfull[buf], (it / kPlaneBufs) & 1, kSpinLimit)) {
+      if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
+      return;
+    }
+    // Diagonal tile: 20 of its 32 sub-tiles of 16 x 8 hold entries with i <= j.
+    // Warps 0-3 take the 32 x 16 pieces (0,1), (0,2), (0,3), (1,3) whole; warps
+    // 4-7 take the single sub-tiles (mi 0, ni 0/1) of pieces (0,0) and (1,2).
+    // Each SM sub-partition (warps w and w+4) then runs 5 sub-tiles.
+    int pwm = wm, pwn = wn, sel = kSelAll;
+    if (diag) {
+      if (warp < 4) {
+        pwm = warp == 3 ? 1 : 0;
+        pwn = warp == 3 ? 3 : warp + 1;
+      } else {
+        pwm = warp >= 6 ? 1 : 0;
+        pwn = warp >= 6 ? 2 : 0;
+        sel = (warp & 1) ? kSel01 : kSel00;
+      }
+    }
+    {
+      const int nvalid = args.T - x.c * kTC;
+      const uint32_t a_base = smem_u32(sm.plane[buf][0][0]);
+      const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
+      const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
+      const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
+      if (sel == kSelAll)
+        chunk_mma<kSelAll>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
+      else if (sel == kSel00)
+        chunk_mma<kSel00>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
+      else
+        chunk_mma<kSel01>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.pempty[buf]);
+    if (x.c + 1 == x.c1) {  // end of the item: write it
+      const int4 w = args.items[x.item];
+      const bool whole = w.z == 0 && w.w == args.nch;
+      const int mode = whole ? (args.fresh ? 0 : 1) : 2;
+      write_piece(args, x.f, x.bi * kTile, x.bj * kTile, pwm, pwn, lane, mode, sel, acc);
+      zero_acc(acc);
+    }
+    x.next();
   }
 }
 

@@ -3,8 +3,8 @@
 
 #include <cstdint>
 
-#include "../../include/xengine.h"
-#include "../../include/xengine_peaks.h"
+#include "xengine.h"
+#include "xengine_peaks.h"
 #include "xe_ptx.cuh"
 
 namespace {

@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/xengine.h"
+#include "xengine.h"
 #include "xe_corr.cuh"
 
 namespace {
@@ -48,7 +48,7 @@ EncodeTiledFn encode_fn() {
 }
 
 // ---- per-device kernel set-up ---------------------------------------------------
-constexpr size_t kSmemBytes = sizeof(xe::CorrSmem) + 1024;  // + alignment slack
+constexpr size_t kSmemBytes = sizeof(xe::CorrSmem) + 128;  // + alignment slack
 std::mutex g_dev_mu;
 int g_blocks_per_sm[64];
 int g_sms[64];
@@ -90,6 +90,13 @@ void triangle_tiles(int32_t N, int32_t tile, std::vector<int32_t>& bi, std::vect
 
 }  // namespace
 
+// A launch schedule: work items (band, tile, chunk range) taken round-robin
+// by the CTAs of one persistent launch.
+struct Plan {
+  int4* d_items = nullptr;  // {f, bi | bj << 16, c0, c1}
+  int32_t nitems = 0, nch = 0, grid = 0, T = 0, split = 1;
+};
+
 // ---- the handle ----------------------------------------------------------------
 struct corr_handle {
   int32_t N = 0, F = 0, T = 0;
@@ -105,21 +112,14 @@ struct corr_handle {
   cudaEvent_t last = nullptr;
   cudaStream_t last_stream = nullptr;
   bool has_last = false;
-  // plan for full frames
-  int4* d_items = nullptr;
-  int32_t num_items = 0;
-  int32_t split = 1;
-  int32_t grid = 0;
+  // schedules (tile list + per-CTA unit ranges) for full frames and the host path's chunks
+  Plan plan, plan_chunk, plan_tail;
   // aligned staging for frames whose rows are not 16-byte aligned
   uint8_t* stage = nullptr;
   size_t stage_bytes = 0;
   // host-input path: two device chunk buffers, two streams
   uint8_t* hchunk[2] = {nullptr, nullptr};
-  int32_t hchunk_T = 0;
-  int4* d_items_chunk = nullptr;
-  int32_t num_items_chunk = 0, split_chunk = 1, grid_chunk = 0;
-  int4* d_items_tail = nullptr;
-  int32_t num_items_tail = 0, split_tail = 1, grid_tail = 0, tail_T = 0;
+  int32_t hchunk_T = 0, tail_T = 0;
   cudaStream_t s_copy = nullptr, s_comp = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
 };
@@ -137,43 +137,102 @@ int cuda_fail(corr_handle* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);       \
   } while (0)
 
-// Build the work list of a frame with T samples: every (band, tile) with the
-// time range split in `split` parts on stage boundaries.
-int build_items(corr_handle* h, int32_t T, int4** d_items, int32_t* num_items, int32_t* split, int32_t* grid) {
+// Relative cost of one chunk of a diagonal tile: its 20 needed 16 x 8
+// sub-tiles run 5 per SM sub-partition (8 on a full tile), a little slower
+// per sub-tile than a full tile's.
+constexpr double kDiagCost = 0.7;
+
+// Tiles of a frame: band-major, row-major over the upper triangle of each band.
+void frame_tiles(int32_t N, int32_t F, std::vector<int2>& tiles, std::vector<double>& cost) {
   std::vector<int32_t> bi, bj;
-  triangle_tiles(h->N, xe::kTile, bi, bj);
-  const int64_t tiles = static_cast<int64_t>(bi.size()) * h->F;
-  const int64_t slots = static_cast<int64_t>(g_sms[h->device]) * g_blocks_per_sm[h->device];
-  const int64_t stages_total = ceil_div(T, xe::kTC);
-  int64_t s = 1;
-  // enough items that the tail of a persistent round-robin stays short
-  if (tiles < 4 * slots) s = std::min<int64_t>(ceil_div(4 * slots, tiles), std::max<int64_t>(1, stages_total / 4));
-  s = std::max<int64_t>(1, std::min<int64_t>(s, stages_total));
-  const int64_t per = ceil_div(stages_total, s) * xe::kTC;  // samples per split, a stage multiple
-  std::vector<int4> items;
-  items.reserve(static_cast<size_t>(tiles * s));
-  // band-major within a split so that one band's tiles run together and share its input in L2;
-  // off-diagonal (full) tiles first in each band, diagonal ones after.
-  for (int64_t k = 0; k < s; ++k) {
-    const int32_t t0 = static_cast<int32_t>(k * per);
-    const int32_t t1 = static_cast<int32_t>(std::min<int64_t>(T, (k + 1) * per));
-    if (t0 >= t1) continue;
-    for (int32_t f = 0; f < h->F; ++f) {
-      for (int pass = 0; pass < 2; ++pass)
-        for (size_t u = 0; u < bi.size(); ++u) {
-          const bool diag = bi[u] == bj[u];
-          if ((pass == 0) == diag) continue;
-          items.push_back(make_int4(f, bi[u] | (bj[u] << 16), t0, t1));
-        }
-    }
+  triangle_tiles(N, xe::kTile, bi, bj);
+  const size_t per_band = bi.size();
+  tiles.resize(per_band * static_cast<size_t>(F));
+  cost.resize(tiles.size());
+  for (size_t u = 0; u < tiles.size(); ++u) {
+    const size_t k = u % per_band;
+    tiles[u] = make_int2(static_cast<int32_t>(u / per_band), bi[k] | (bj[k] << 16));
+    cost[u] = bi[k] == bj[k] ? kDiagCost : 1.0;
   }
-  if (items.size() > static_cast<size_t>(INT32_MAX)) return fail(CORR_EINVAL, "work list too long");
-  XE_CHECK(h, cudaMalloc(d_items, items.size() * sizeof(int4)));
-  XE_CHECK(h, cudaMemcpy(*d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  *num_items = static_cast<int32_t>(items.size());
-  *split = static_cast<int32_t>(s);
-  *grid = static_cast<int32_t>(std::min<int64_t>(static_cast<int64_t>(items.size()), slots));
+}
+
+// Items of a frame: the time axis cut into `split` ranges of whole chunks
+// (split-major), each range over every tile in frame order. CTA k of P takes
+// items k, k+P, ... so the CTAs running together work on neighbouring tiles
+// of one band over the same time range and share its input in L2.
+void make_items(const std::vector<int2>& tiles, int64_t nch, int64_t split, std::vector<int4>& items) {
+  items.clear();
+  const int64_t per = ceil_div(nch, split);
+  for (int64_t k = 0; k < split; ++k) {
+    const int64_t c0 = k * per, c1 = std::min<int64_t>(nch, (k + 1) * per);
+    if (c0 >= c1) continue;
+    for (const int2& t : tiles)
+      items.push_back(make_int4(t.x, t.y, static_cast<int32_t>(c0), static_cast<int32_t>(c1)));
+  }
+}
+
+// Largest per-CTA cost over the mean under round-robin assignment.
+double imbalance(const std::vector<int4>& items, const std::vector<double>& cost_of_tile, int64_t ntiles, int64_t P) {
+  std::vector<double> load(static_cast<size_t>(P), 0.0);
+  double total = 0.0;
+  for (size_t k = 0; k < items.size(); ++k) {
+    const double c = cost_of_tile[k % ntiles] * (items[k].w - items[k].z);
+    load[k % P] += c;
+    total += c;
+  }
+  const double mean = total / static_cast<double>(P);
+  return *std::max_element(load.begin(), load.end()) / mean;
+}
+
+// Pick the time split: the smallest that keeps the busiest CTA within 3% of
+// the mean (whole tiles need no atomics), else the best of the candidates.
+void plan_items(int32_t N, int32_t F, int32_t T, int64_t slots, std::vector<int4>& items, int64_t* split_out,
+                int64_t* grid_out) {
+  std::vector<int2> tiles;
+  std::vector<double> cost;
+  frame_tiles(N, F, tiles, cost);
+  const int64_t ntiles = static_cast<int64_t>(tiles.size());
+  const int64_t nch = ceil_div(T, xe::kTC);
+  int64_t best_split = 1;
+  double best = 1e30;
+  for (int64_t split : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+    if (split > nch) break;
+    std::vector<int4> cand;
+    make_items(tiles, nch, split, cand);
+    const int64_t P = std::min<int64_t>(slots, static_cast<int64_t>(cand.size()));
+    // a launch narrower than the GPU runs at P/slots of its speed
+    const double eff = imbalance(cand, cost, ntiles, P) * static_cast<double>(slots) / static_cast<double>(P);
+    if (eff < best - 1e-9) {
+      best = eff;
+      best_split = split;
+    }
+    if (eff <= 1.03) break;
+  }
+  make_items(tiles, nch, best_split, items);
+  *split_out = best_split;
+  *grid_out = std::min<int64_t>(slots, static_cast<int64_t>(items.size()));
+}
+
+// Schedule a frame of T samples for the resident CTAs of this device.
+int build_plan(corr_handle* h, int32_t T, Plan* pl) {
+  const int64_t slots = static_cast<int64_t>(g_sms[h->device]) * g_blocks_per_sm[h->device];
+  std::vector<int4> items;
+  int64_t split = 1, grid = 1;
+  plan_items(h->N, h->F, T, slots, items, &split, &grid);
+  if (items.size() > static_cast<size_t>(INT32_MAX)) return fail(CORR_EINVAL, "schedule too large");
+  XE_CHECK(h, cudaMalloc(&pl->d_items, items.size() * sizeof(int4)));
+  XE_CHECK(h, cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  pl->nitems = static_cast<int32_t>(items.size());
+  pl->nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
+  pl->grid = static_cast<int32_t>(grid);
+  pl->T = T;
+  pl->split = static_cast<int32_t>(split);
   return CORR_OK;
+}
+
+void free_plan(Plan* pl) {
+  if (pl->d_items) cudaFree(pl->d_items);
+  *pl = Plan();
 }
 
 int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_t T) {
@@ -210,27 +269,23 @@ int check_handle(corr_handle* h) {
 }
 
 // Launch the correlator over a [T][F][Np] device frame (16-byte aligned rows).
-int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, int32_t T, const int4* items, int32_t nitems,
-                 int32_t split, int32_t grid, cudaStream_t st) {
+int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& pl, cudaStream_t st) {
   CUtensorMap tm;
-  int rc = make_tmap(&tm, frame, Np, h->F, T);
+  int rc = make_tmap(&tm, frame, Np, h->F, pl.T);
   if (rc) return rc;
-  int mode;
-  if (split == 1) {
-    mode = h->fresh ? xe::kStore : xe::kAdd;
-  } else {
-    if (h->fresh) XE_CHECK(h, cudaMemsetAsync(h->acc, 0, static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t), st));
-    mode = xe::kRed;
-  }
+  if (h->fresh && pl.split > 1)  // time-split items add atomically onto zeros
+    XE_CHECK(h, cudaMemsetAsync(h->acc, 0, static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t), st));
   xe::CorrArgs a;
-  a.items = items;
-  a.num_items = nitems;
+  a.items = pl.d_items;
+  a.nitems = pl.nitems;
+  a.nch = pl.nch;
+  a.T = pl.T;
   a.N = h->N;
   a.B = h->B;
   a.vis = h->acc;
-  a.mode = mode;
+  a.fresh = h->fresh ? 1 : 0;
   a.err = h->d_err;
-  xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  xe::corr_tile_kernel<<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
   ++h->launches;
   h->fresh = false;
@@ -279,7 +334,7 @@ corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
   if (ok && cudaMemset(h->d_err, 0, sizeof(int32_t)) != cudaSuccess) ok = !fail(CORR_ECUDA, "memset error word");
   if (ok && cudaEventCreateWithFlags(&h->last, cudaEventDisableTiming) != cudaSuccess)
     ok = !fail(CORR_ECUDA, "cudaEventCreate failed");
-  if (ok && build_items(h, T, &h->d_items, &h->num_items, &h->split, &h->grid) != CORR_OK) ok = false;
+  if (ok && build_plan(h, T, &h->plan) != CORR_OK) ok = false;
   if (!ok) {
     std::string msg = g_last_error;
     corr_destroy(h);
@@ -348,7 +403,7 @@ int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream) {
   const uint8_t* frame;
   int32_t np;
   if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np))) return rc;
-  if ((rc = launch_frame(h, frame, np, h->T, h->d_items, h->num_items, h->split, h->grid, st))) return rc;
+  if ((rc = launch_frame(h, frame, np, h->plan, st))) return rc;
   h->samples += h->T;
   return record_last(h, st);
 }
@@ -380,12 +435,9 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
     XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     XE_CHECK(h, cudaStreamCreateWithFlags(&h->s_copy, cudaStreamNonBlocking));
     XE_CHECK(h, cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking));
-    if ((rc = build_items(h, h->hchunk_T, &h->d_items_chunk, &h->num_items_chunk, &h->split_chunk, &h->grid_chunk)))
-      return rc;
+    if ((rc = build_plan(h, h->hchunk_T, &h->plan_chunk))) return rc;
     h->tail_T = h->T % h->hchunk_T;
-    if (h->tail_T &&
-        (rc = build_items(h, h->tail_T, &h->d_items_tail, &h->num_items_tail, &h->split_tail, &h->grid_tail)))
-      return rc;
+    if (h->tail_T && (rc = build_plan(h, h->tail_T, &h->plan_tail))) return rc;
   }
   // internal streams start after everything already queued on `st` (and the handle's last call)
   if ((rc = order_after_last(h, st))) return rc;
@@ -408,10 +460,7 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
     XE_CHECK(h, cudaEventRecord(h->ev_copied[b], h->s_copy));
     XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_copied[b], 0));
     const bool tail = cT != h->hchunk_T;
-    if ((rc = launch_frame(h, h->hchunk[b], Np, cT, tail ? h->d_items_tail : h->d_items_chunk,
-                           tail ? h->num_items_tail : h->num_items_chunk, tail ? h->split_tail : h->split_chunk,
-                           tail ? h->grid_tail : h->grid_chunk, h->s_comp)))
-      return rc;
+    if ((rc = launch_frame(h, h->hchunk[b], Np, tail ? h->plan_tail : h->plan_chunk, h->s_comp))) return rc;
     XE_CHECK(h, cudaEventRecord(h->ev_used[b], h->s_comp));
   }
   // the caller's stream continues after the last chunk
@@ -518,9 +567,9 @@ void corr_destroy(corr_handle_t* h) {
   if (h->has_last) cudaEventSynchronize(h->last);
   if (h->own_acc && h->acc) cudaFree(h->acc);
   if (h->d_err) cudaFree(h->d_err);
-  if (h->d_items) cudaFree(h->d_items);
-  if (h->d_items_chunk) cudaFree(h->d_items_chunk);
-  if (h->d_items_tail) cudaFree(h->d_items_tail);
+  free_plan(&h->plan);
+  free_plan(&h->plan_chunk);
+  free_plan(&h->plan_tail);
   if (h->stage) cudaFree(h->stage);
   for (int k = 0; k < 2; ++k) {
     if (h->hchunk[k]) cudaFree(h->hchunk[k]);
@@ -544,6 +593,23 @@ int64_t corr_plan_tiles(int32_t N, int32_t tile, int32_t* bi_out, int32_t* bj_ou
     if (bj_out) bj_out[k] = bj[k];
   }
   return n;
+}
+
+int64_t corr_plan_schedule(int32_t N, int32_t F, int32_t T, int32_t ctas, int32_t* items_out, int64_t items_cap,
+                           int32_t* grid_out) {
+  if (N < 1 || N > CORR_MAX_N || F < 1 || T < 1 || ctas < 1) return fail(CORR_EINVAL, "bad schedule query");
+  std::vector<int4> items;
+  int64_t split = 1, grid = 1;
+  plan_items(N, F, T, ctas, items, &split, &grid);
+  if (items_out)
+    for (int64_t k = 0; k < static_cast<int64_t>(items.size()) && k < items_cap; ++k) {
+      items_out[4 * k] = items[k].x;
+      items_out[4 * k + 1] = items[k].y;
+      items_out[4 * k + 2] = items[k].z;
+      items_out[4 * k + 3] = items[k].w;
+    }
+  if (grid_out) *grid_out = static_cast<int32_t>(grid);
+  return static_cast<int64_t>(items.size());
 }
 
 double corr_effective_ops(int32_t N, int32_t F, int32_t T) {

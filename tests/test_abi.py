@@ -93,3 +93,28 @@ def test_null_handle_calls(xe):
     assert L.corr_status(None) == CORR_EINVAL
     L.corr_destroy(None)  # NULL-safe
     assert b"NULL" in L.corr_last_error()
+
+
+@pytest.mark.parametrize("N,F,T,ctas", [(256, 256, 16384, 152), (8192, 4, 2048, 152), (16, 4, 256, 152),
+                                        (1, 1, 1, 152), (100, 3, 300, 7), (64, 2, 8192, 152), (2048, 5, 777, 152)])
+def test_schedule_covers_every_unit_once(xe, N, F, T, ctas):
+    """Every (tile, time chunk) is computed by exactly one item; CTAs get balanced work."""
+    import numpy as np
+    items, grid = xe.plan_schedule(N, F, T, ctas)
+    nb = -(-N // 64)
+    per_band = nb * (nb + 1) // 2
+    nch = -(-T // 64)
+    assert 1 <= grid <= ctas
+    f, bi, bj, c0, c1 = items[:, 0], items[:, 1] & 0xFFFF, items[:, 1] >> 16, items[:, 2], items[:, 3]
+    assert (bi <= bj).all() and (bj < nb).all() and (f < F).all() and (0 <= c0).all() and (c0 < c1).all()
+    assert (c1 <= nch).all()
+    seen = np.zeros((F, nb, nb, nch), dtype=np.int32)
+    for k in range(len(items)):
+        seen[f[k], bi[k], bj[k], c0[k]:c1[k]] += 1
+    iu, ju = np.triu_indices(nb)
+    assert (seen[:, iu, ju, :] == 1).all()
+    assert seen.sum() == F * per_band * nch
+    cost = np.where(bi == bj, 0.75, 1.0) * (c1 - c0)
+    load = np.bincount(np.arange(len(items)) % grid, weights=cost, minlength=grid)
+    if len(items) >= 4 * grid:
+        assert load.max() <= 1.06 * load.mean()
