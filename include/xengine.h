@@ -171,6 +171,36 @@ int64_t corr_plan_schedule(int32_t N, int32_t F, int32_t T, int32_t ctas, int32_
  */
 double corr_effective_ops(int32_t N, int32_t F, int32_t T);
 
+/*
+ * corr_correlate_noalloc -- correlate one frame without allocating anything.
+ * (The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory when they correlate: code running while a stream
+ * is captured into a CUDA graph, where cudaMalloc/cudaFree are not allowed;
+ * applications whose device memory belongs to their own pool allocator; and
+ * real-time hosts that reserve all memory up front.)
+ *
+ * packed_dev: device frame uint8 x[T][F][N] (layout above); N must be a
+ *   multiple of 16 and the pointer 16-byte aligned (no staging copy here).
+ * vis_dev: device output int32 [F][N(N+1)/2][2], overwritten with this
+ *   frame's visibilities (a fresh integration: nothing is added to it).
+ * status_dev: NULL, or a device int32 that receives 0, or a nonzero fault
+ *   code if a bounded wait inside the kernel ran out.
+ * The kernel's work list and fault word live in a fixed array of 65,536
+ * work items (1 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits. Frames with more than 65,536
+ * tiles of 64 x 64 (N(N+1)/2-triangle tiles times F) return CORR_EINVAL
+ * without launching anything. The call uses no cudaMalloc, cudaFree or other
+ * allocating routine; on success it touches no allocator at all (a failure
+ * records its message for corr_last_error). Asynchronous on `stream`.
+ * The first call on each device looks up the array's device address and
+ * sets the kernel's shared-memory limit; make that first call before any
+ * stream capture. All calls share the one array and each call rewrites it,
+ * so calls that can overlap on the GPU (different streams, no ordering
+ * between them) race and must not be issued; calls on one stream are safe.
+ */
+int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int32_t F, int32_t T, int32_t* vis_dev,
+                           int32_t* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_
                    XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "plan_schedule", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "correlate_noalloc", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -159,6 +159,23 @@ class Correlator:
     @property
     def handle(self):
         return self._h
+
+
+def correlate_noalloc(x, out, status=None, stream=None):
+    """One frame into `out` (int32 [F][N(N+1)/2][2], overwritten) with no allocation by the library.
+
+    For callers that cannot allocate device memory at call time (graph capture,
+    a foreign pool allocator, real-time hosts): the work list lives in a fixed
+    1 MiB array inside the library. `x` is a contiguous CUDA uint8 [T][F][N]
+    tensor with N a multiple of 16; `status`, if given, is a CUDA int32 tensor
+    that receives the kernel's fault word (0 = no fault). Calls that may overlap
+    on the GPU race on the shared array; keep them on one stream.
+    """
+    T, F, N = x.shape
+    check(lib().corr_correlate_noalloc(ctypes.c_void_p(x.data_ptr()), N, F, T, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(status.data_ptr()) if status is not None else None,
+                                       _stream_ptr(stream)))
+    return out
 
 
 def accumulate_batch(correlators, inputs, stream=None):

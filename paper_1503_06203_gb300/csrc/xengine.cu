@@ -617,3 +617,122 @@ double corr_effective_ops(int32_t N, int32_t F, int32_t T) {
 }
 
 }  // extern "C"
+
+// =============================================================================
+// Allocation-free correlation of one frame (corr_correlate_noalloc).
+//
+// Some callers cannot allocate device memory when they need a correlation:
+// code that runs while a stream is being captured into a CUDA graph (where
+// cudaMalloc and cudaFree are not allowed), applications whose device memory
+// belongs to their own pool allocator and may not be taken behind its back,
+// and real-time hosts that reserve every byte up front and forbid allocations
+// on the processing path. corr_correlate_noalloc serves them: the caller
+// passes the frame and the output buffer, and the only other device memory the
+// kernel needs (its work list and its fault word) is the fixed array below.
+// Every GPU that loads this library holds that array until the process exits.
+// =============================================================================
+namespace {
+
+// Work items the fixed array can hold: 65,536 (1 MiB), enough for N = 8192 at
+// F = 7 or N = 2048 at F = 124 with whole tiles. Element 0 holds the fault word.
+constexpr int64_t kNoAllocMaxItems = 65536;
+static __device__ __align__(256) int4 g_noalloc_scratch[1 + kNoAllocMaxItems];
+
+std::mutex g_noalloc_mu;
+int4* g_noalloc_addr[64];  // device address of g_noalloc_scratch, per device
+
+// Writes the frame's work list: item k = split s, tile u of the frame (bands
+// outermost, each band's upper triangle row by row), chunks [s*per, ...).
+__global__ void noalloc_plan_kernel(int4* items, int32_t nb, int32_t F, int32_t nch, int32_t per, int64_t nitems) {
+  const int64_t per_band = static_cast<int64_t>(nb) * (nb + 1) / 2;
+  const int64_t ntiles = per_band * F;
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < nitems;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t s = k / ntiles, u = k % ntiles;
+    const int32_t f = static_cast<int32_t>(u / per_band);
+    int64_t q = u % per_band;
+    int32_t bi = 0;
+    while (q >= nb - bi) {  // row bi of the triangle holds nb - bi tiles
+      q -= nb - bi;
+      ++bi;
+    }
+    const int32_t bj = bi + static_cast<int32_t>(q);
+    const int32_t c0 = static_cast<int32_t>(s * per);
+    const int32_t c1 = static_cast<int32_t>(min(static_cast<int64_t>(nch), (s + 1) * per));
+    items[k] = make_int4(f, bi | (bj << 16), c0, c1);
+  }
+}
+
+// Once per device, with that device current: the array's device address.
+int noalloc_setup(int dev, int4** addr) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<int4*>(p);
+  }
+  *addr = g_noalloc_addr[dev];
+  return CORR_OK;
+}
+
+}  // namespace
+
+extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int32_t F, int32_t T, int32_t* vis_dev,
+                                      int32_t* status_dev, void* stream) {
+  if (!packed_dev || !vis_dev) return fail(CORR_EINVAL, "noalloc: NULL input or output");
+  if (N < 1 || N > CORR_MAX_N || F < 1 || T < 1 || T > CORR_MAX_SAMPLES)
+    return fail(CORR_EINVAL, "noalloc: N=%d F=%d T=%d out of range", N, F, T);
+  if (N % 16 != 0 || (reinterpret_cast<uintptr_t>(packed_dev) & 15) != 0)
+    return fail(CORR_EINVAL, "noalloc: needs N a multiple of 16 and a 16-byte aligned frame (N=%d)", N);
+  const int64_t nb = ceil_div(N, xe::kTile);
+  const int64_t ntiles = nb * (nb + 1) / 2 * F;
+  const int64_t nch = ceil_div(T, xe::kTC);
+  if (ntiles > kNoAllocMaxItems)
+    return fail(CORR_EINVAL, "noalloc: %lld tiles exceed the fixed work-list size of %lld items",
+                static_cast<long long>(ntiles), static_cast<long long>(kNoAllocMaxItems));
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  int rc = device_setup(dev);
+  if (rc) return rc;
+  int4* scratch = nullptr;
+  if ((rc = noalloc_setup(dev, &scratch))) return rc;
+  const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
+  // time split: enough items to keep every CTA busy, within the array and the frame's chunks
+  int64_t split = std::min<int64_t>({ceil_div(4 * slots, ntiles), kNoAllocMaxItems / ntiles, nch, int64_t(64)});
+  split = std::max<int64_t>(split, 1);
+  const int64_t per = ceil_div(nch, split);
+  split = ceil_div(nch, per);  // no empty ranges
+  const int64_t nitems = ntiles * split;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t vis_bytes = static_cast<size_t>(F) * (static_cast<size_t>(N) * (N + 1) / 2) * 2 * sizeof(int32_t);
+  // the fault word starts at zero; time-split items add atomically onto a zeroed output
+  if ((e = cudaMemsetAsync(scratch, 0, sizeof(int4), st)) != cudaSuccess)
+    return fail(CORR_ECUDA, "noalloc: clearing the fault word: %s", cudaGetErrorString(e));
+  if (split > 1 && (e = cudaMemsetAsync(vis_dev, 0, vis_bytes, st)) != cudaSuccess)
+    return fail(CORR_ECUDA, "noalloc: clearing the output: %s", cudaGetErrorString(e));
+  const int pb = static_cast<int>(std::min<int64_t>(ceil_div(nitems, 256), 1024));
+  noalloc_plan_kernel<<<pb, 256, 0, st>>>(scratch + 1, static_cast<int32_t>(nb), F, static_cast<int32_t>(nch),
+                                          static_cast<int32_t>(per), nitems);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(CORR_ECUDA, "noalloc plan: %s", cudaGetErrorString(e));
+  CUtensorMap tm;
+  if ((rc = make_tmap(&tm, packed_dev, N, F, T))) return rc;
+  xe::CorrArgs a;
+  a.items = scratch + 1;
+  a.nitems = static_cast<int32_t>(nitems);
+  a.nch = static_cast<int32_t>(nch);
+  a.T = T;
+  a.N = N;
+  a.B = static_cast<int64_t>(N) * (N + 1) / 2;
+  a.vis = vis_dev;
+  a.fresh = 1;
+  a.err = reinterpret_cast<int32_t*>(scratch);
+  const int grid = static_cast<int>(std::min<int64_t>(slots, nitems));
+  xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(CORR_ECUDA, "noalloc correlate: %s", cudaGetErrorString(e));
+  if (status_dev && (e = cudaMemcpyAsync(status_dev, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) !=
+                        cudaSuccess)
+    return fail(CORR_ECUDA, "noalloc: copying the fault word: %s", cudaGetErrorString(e));
+  return CORR_OK;
+}
