@@ -33,7 +33,7 @@ constexpr int kTC = 64;                    // time samples per chunk (pipeline s
 #endif
 constexpr int kStages = XE_STAGES;         // TMA ring depth
 constexpr int kPlaneBufs = XE_PLANE_BUFS;  // unpacked-plane buffers between the unpack and product warps
-constexpr int kMmaWarps = 8;               // product warps: 2 x 4 warps of 32 x 16
+constexpr int kMmaWarps = 16;              // product warps: 4 x 4 warps of 16 x 16
 constexpr int kUnpackThreads = 128;        // unpack warpgroup
 constexpr int kThreads = kMmaWarps * 32 + kUnpackThreads;
 constexpr int kBoxBytes = kTile * kTC;     // packed box: [time][element] bytes
@@ -55,6 +55,7 @@ struct CorrArgs {
   int64_t B;            // N(N+1)/2
   int32_t* vis;         // [F][B][2] accumulators
   int32_t fresh;        // 1: accumulators hold no integration yet (whole tiles store)
+  int32_t hybrid;       // 1: samples 32..63 of each chunk run on dp4a (chunk_hybrid), 0: tensor cores only
   int32_t* err;         // device error word
 };
 
@@ -134,26 +135,32 @@ __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint8_t* pl0, ui
   }
 }
 
-// ---- product: one 64-sample chunk of a warp's 32 x 16 piece of the tile --------
-// acc[0] = P1, acc[1] = P2, acc[2] = Q, each over the piece's 2 x 2 sub-tiles
-// of 16 x 8. Planes are addressed as shared-memory offsets: A side slot p at
-// a_base + p*kPlaneBytes; B side slots 0-1 at b01_base + p*kPlaneBytes and
-// slot 2 at b2_base (on a diagonal tile the B side's xr, xi planes are the A
-// side's).
-//
-// Sub-tile selection: kSelAll = the whole piece; kSel00 / kSel01 = only the
-// sub-tile (mi = 0, ni = 0 / 1) (used on diagonal tiles, see the kernel).
-enum : int { kSelAll = 0, kSel00 = 1, kSel01 = 2 };
+// ---- product: one 64-sample chunk of a warp's 16 x 16 piece of the tile --------
+// acc[0] = P1, acc[1] = P2, acc[2] = Q, each over the piece's two 16 x 8
+// sub-tiles (ni = 0, 1). Planes are addressed as shared-memory offsets: A side
+// slot p at a_base + p*kPlaneBytes; B side slots 0-1 at b01_base +
+// p*kPlaneBytes and slot 2 at b2_base (on a diagonal tile the B side's xr, xi
+// planes are the A side's). Sub-tile selection: kSelAll = both sub-tiles,
+// kSelN0 / kSelN1 = only sub-tile 0 / 1 (used on diagonal tiles, see the kernel).
+enum : int { kSelAll = 0, kSelN0 = 1, kSelN1 = 2, kSelIdle = 3 };
 
-__device__ __forceinline__ constexpr bool sub_on(int sel, int mi, int ni) {
-  return sel == kSelAll || (mi == 0 && ni == sel - 1);
+__device__ __forceinline__ constexpr bool sub_on(int sel, int ni) { return sel == kSelAll || ni == sel - 1; }
+
+__device__ __forceinline__ void zero_acc(int32_t (&acc)[3][2][4]) {
+#pragma unroll
+  for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[pl][ni][r] = 0;
 }
 
+// Tensor cores only, k-steps [0, ksteps) of the chunk.
 template <int sel>
-__device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pwm, int pwn,
-                                          int lane, int ksteps, int32_t (&acc)[3][2][2][4]) {
-  const int arow = pwm * 32 + (lane & 15);
-  const int brow = pwn * 16 + (lane & 7) + ((lane >> 4) << 3);
+__device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
+                                          int lane, int ksteps, int32_t (&acc)[3][2][4]) {
+  const int arow = pr * 16 + (lane & 15);
+  const int brow = pc * 16 + (lane & 7) + ((lane >> 4) << 3);
   const int ahalf = lane >> 4, bhalf = (lane >> 3) & 1;
 #pragma unroll
   for (int ks = 0; ks < kTC / 32; ++ks) {
@@ -162,19 +169,69 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
     for (int pl = 0; pl < 3; ++pl) {
       const uint32_t pa = a_base + pl * kPlaneBytes;
       const uint32_t pb = pl < 2 ? b01_base + pl * kPlaneBytes : b2_base;
-      uint32_t a[2][4], b[2][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-        if (sel == kSelAll || mi == 0)
-          ldsm_x4(pa + plane_off(arow + mi * 16, 2 * ks + ahalf), a[mi][0], a[mi][1], a[mi][2], a[mi][3]);
+      uint32_t a[4], b[2][2];
+      ldsm_x4(pa + plane_off(arow, 2 * ks + ahalf), a[0], a[1], a[2], a[3]);
       ldsm_x4(pb + plane_off(brow, 2 * ks + bhalf), b[0][0], b[0][1], b[1][0], b[1][1]);
 #pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni)
-          if (sub_on(sel, mi, ni))
-            mma_s8_16832(acc[pl][mi][ni], a[mi][0], a[mi][1], a[mi][2], a[mi][3], b[ni][0], b[ni][1]);
+      for (int ni = 0; ni < 2; ++ni)
+        if (sub_on(sel, ni)) mma_s8_16832(acc[pl][ni], a[0], a[1], a[2], a[3], b[ni][0], b[ni][1]);
     }
+  }
+}
+
+// ---- product, hybrid: tensor cores and the integer ALU side by side -----------
+// The tensor pipe and the dp4a pipe of an SM sub-partition run concurrently
+// and at about the same rate on this GPU. A warp runs the three products for
+// samples 0..31 of the chunk on the tensor cores (one k-step) and for samples
+// 32..63 with dp4a (4 samples per instruction), accumulating both into the
+// same registers: thread (g, q) owns, per sub-tile ni, the entries (row
+// g + 8h, column ni*8 + 2q + c) of the MMA accumulator layout, so its dp4a
+// work is those entries' dot products. Each of the 6 blocks below issues one
+// MMA (plane k/2, sub-tile k%2) and 32 dp4a (8 samples of one plane).
+template <int sel>
+__device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
+                                             int lane, int32_t (&acc)[3][2][4]) {
+  constexpr int kNi0 = sel == kSelN1 ? 1 : 0;  // first column sub-tile
+  constexpr int kNi = sel == kSelAll ? 2 : 1;   // column sub-tiles
+  const int g = lane >> 2, q = lane & 3;
+  const int arow = pr * 16 + (lane & 15);
+  const int brow = pc * 16 + (lane & 7) + ((lane >> 4) << 3);
+  const int ahalf = lane >> 4, bhalf = (lane >> 3) & 1;
+  uint32_t fa[4], fb[2][2];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    // ---- tensor cores: k-step 0 (samples 0..31), one MMA every other block ----
+    if ((k & 1) == 0) {
+      const int mk = k >> 1, mpl = mk >> 1, mni = mk & 1;
+      if (mni == 0) {
+        const uint32_t pa = a_base + mpl * kPlaneBytes;
+        const uint32_t pb = mpl < 2 ? b01_base + mpl * kPlaneBytes : b2_base;
+        ldsm_x4(pa + plane_off(arow, ahalf), fa[0], fa[1], fa[2], fa[3]);
+        ldsm_x4(pb + plane_off(brow, bhalf), fb[0][0], fb[0][1], fb[1][0], fb[1][1]);
+      }
+      if (sub_on(sel, mni)) mma_s8_16832(acc[mpl][mni], fa[0], fa[1], fa[2], fa[3], fb[mni][0], fb[mni][1]);
+    }
+    // ---- integer ALU: samples 32 + 8*grp .. +7 of plane dpl ----
+    const int grp = k / 3, dpl = k % 3;
+    const int s0 = 32 + 8 * grp, chunk = s0 >> 4, inner = s0 & 15;
+    const uint32_t pa = a_base + dpl * kPlaneBytes;
+    const uint32_t pb = dpl < 2 ? b01_base + dpl * kPlaneBytes : b2_base;
+    uint32_t av[2][2], bv[2][2][2];  // [h][word], [n][c][word]
+#pragma unroll
+    for (int h = 0; h < 2; ++h) lds64(pa + plane_off(pr * 16 + g + 8 * h, chunk) + inner, av[h][0], av[h][1]);
+#pragma unroll
+    for (int n = 0; n < kNi; ++n)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+        lds64(pb + plane_off(pc * 16 + (kNi0 + n) * 8 + 2 * q + c, chunk) + inner, bv[n][c][0], bv[n][c][1]);
+#pragma unroll
+    for (int wd = 0; wd < 2; ++wd)
+#pragma unroll
+      for (int n = 0; n < kNi; ++n)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) dp4a_acc(acc[dpl][kNi0 + n][2 * h + c], av[h][wd], bv[n][c][wd]);
   }
 }
 
@@ -184,53 +241,49 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // whose other parts other CTAs add). Entries with i > j, outside the N x N
 // matrix, or in sub-tiles the warp did not compute are dropped; entry (i, j)
 // of band f lives at (f*B + p(i,j))*2, p(i,j) = i*N - i(i-1)/2 + j - i.
-__device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, int j0, int pwm, int pwn, int lane,
-                                            int mode, int sel, int32_t (&acc)[3][2][2][4]) {
+__device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, int j0, int pr, int pc, int lane,
+                                            int mode, int sel, int32_t (&acc)[3][2][4]) {
   // fold in place: Re = P1 + P2 into acc[0], Im = Q - P1 + P2 into acc[2] (modulo 2^32;
   // exact for in-range Re, Im)
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const uint32_t p1 = static_cast<uint32_t>(acc[0][mi][ni][r]), p2 = static_cast<uint32_t>(acc[1][mi][ni][r]);
-        acc[0][mi][ni][r] = static_cast<int32_t>(p1 + p2);
-        acc[2][mi][ni][r] = static_cast<int32_t>(static_cast<uint32_t>(acc[2][mi][ni][r]) - p1 + p2);
-      }
+    for (int r = 0; r < 4; ++r) {
+      const uint32_t p1 = static_cast<uint32_t>(acc[0][ni][r]), p2 = static_cast<uint32_t>(acc[1][ni][r]);
+      acc[0][ni][r] = static_cast<int32_t>(p1 + p2);
+      acc[2][ni][r] = static_cast<int32_t>(static_cast<uint32_t>(acc[2][ni][r]) - p1 + p2);
+    }
   const int g = lane >> 2, q = lane & 3;
   const int N = a.N;
   int32_t* base = a.vis + static_cast<int64_t>(f) * a.B * 2;
-  const int jw = j0 + pwn * 16 + 2 * q;
+  const int jw = j0 + pc * 16 + 2 * q;
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int h = 0; h < 2; ++h) {
+    const int i = i0 + pr * 16 + g + 8 * h;
+    if (i >= N) continue;
+    const int64_t ii = i;
+    int32_t* rowp = base + (ii * N - ii * (ii - 1) / 2 - ii) * 2;  // entry (i, j) at rowp + 2j
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int i = i0 + pwm * 32 + mi * 16 + g + 8 * h;
-      if (i >= N || (sel != kSelAll && mi != 0)) continue;
-      const int64_t ii = i;
-      int32_t* rowp = base + (ii * N - ii * (ii - 1) / 2 - ii) * 2;  // entry (i, j) at rowp + 2j
+    for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int j = jw + ni * 8 + c;
-          if (j < i || j >= N || (sel != kSelAll && ni != sel - 1)) continue;
-          const int32_t re = acc[0][mi][ni][2 * h + c], im = acc[2][mi][ni][2 * h + c];
-          int32_t* dst = rowp + 2 * j;
-          if (mode == 0) {
-            *reinterpret_cast<int2*>(dst) = make_int2(re, im);
-          } else if (mode == 1) {
-            int2 v = *reinterpret_cast<int2*>(dst);
-            v.x = static_cast<int32_t>(static_cast<uint32_t>(v.x) + static_cast<uint32_t>(re));
-            v.y = static_cast<int32_t>(static_cast<uint32_t>(v.y) + static_cast<uint32_t>(im));
-            *reinterpret_cast<int2*>(dst) = v;
-          } else {
-            atomicAdd(dst, re);
-            atomicAdd(dst + 1, im);
-          }
+      for (int c = 0; c < 2; ++c) {
+        const int j = jw + ni * 8 + c;
+        if (j < i || j >= N || !sub_on(sel, ni)) continue;
+        const int32_t re = acc[0][ni][2 * h + c], im = acc[2][ni][2 * h + c];
+        int32_t* dst = rowp + 2 * j;
+        if (mode == 0) {
+          *reinterpret_cast<int2*>(dst) = make_int2(re, im);
+        } else if (mode == 1) {
+          int2 v = *reinterpret_cast<int2*>(dst);
+          v.x = static_cast<int32_t>(static_cast<uint32_t>(v.x) + static_cast<uint32_t>(re));
+          v.y = static_cast<int32_t>(static_cast<uint32_t>(v.y) + static_cast<uint32_t>(im));
+          *reinterpret_cast<int2*>(dst) = v;
+        } else {
+          atomicAdd(dst, re);
+          atomicAdd(dst + 1, im);
         }
-    }
+      }
+  }
 }
 
 // ---- the kernel ------------------------------------------------------------------
@@ -239,21 +292,10 @@ __device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, in
 // at the same time work on the tiles of one band over the same time chunks
 // and share that band's input in L2.
 //
-// Warp roles. Warps 0-7: tensor-core product and writer, 2 x 4 warps of
-// 32 x 16 (three int32 accumulator sets, 48 registers a thread); two of them
-// share each SM sub-partition. Warps 8-11: unpack; lane 0 of warp 8 also
-// issues the TMA loads. One CTA per SM.
-__device__ __forceinline__ void zero_acc(int32_t (&acc)[3][2][2][4]) {
-#pragma unroll
-  for (int pl = 0; pl < 3; ++pl)
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-      for (int ni = 0; ni < 2; ++ni)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[pl][mi][ni][r] = 0;
-}
-
+// Warp roles. Warps 0-15: product and writer, 4 x 4 warps of 16 x 16 pieces
+// (three int32 accumulator sets, 24 registers a thread); four of them share
+// each SM sub-partition. Warps 16-19: unpack; lane 0 of warp 16 also issues
+// the TMA loads. One CTA per SM.
 // Walks (item, chunk) pairs of this CTA in order.
 struct Walk {
   int item, c, f, bi, bj, c1;
@@ -375,8 +417,15 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   }
 
   // ================= product warps =================
-  const int wm = warp >> 2, wn = warp & 3;
-  int32_t acc[3][2][2][4];
+  // Off-diagonal tile: warp w takes piece (w / 4, w % 4); warps w, w+4, w+8,
+  // w+12 share SM sub-partition w % 4.
+  // Diagonal tile: the 10 pieces on or above the diagonal hold its 20 needed
+  // 16 x 8 sub-tiles. Eight pieces go whole to warps 0-7; pieces (2,2) and
+  // (3,3) are split into single sub-tiles for warps 8-11; warps 12-15 idle.
+  // Each sub-partition then runs 5 sub-tiles (8 on a full tile).
+  // (2 bits per warp: piece row, piece column, selection)
+  constexpr uint32_t kDiagR = 0xfa9050u, kDiagC = 0xfaedd8u, kDiagSel = 0xff990000u;
+  int32_t acc[3][2][4];
   zero_acc(acc);
   uint32_t it = 0;
   Walk x;
@@ -387,33 +436,29 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
       return;
     }
-    // Diagonal tile: 20 of its 32 sub-tiles of 16 x 8 hold entries with i <= j.
-    // Warps 0-3 take the 32 x 16 pieces (0,1), (0,2), (0,3), (1,3) whole; warps
-    // 4-7 take the single sub-tiles (mi 0, ni 0/1) of pieces (0,0) and (1,2).
-    // Each SM sub-partition (warps w and w+4) then runs 5 sub-tiles.
-    int pwm = wm, pwn = wn, sel = kSelAll;
-    if (diag) {
-      if (warp < 4) {
-        pwm = warp == 3 ? 1 : 0;
-        pwn = warp == 3 ? 3 : warp + 1;
-      } else {
-        pwm = warp >= 6 ? 1 : 0;
-        pwn = warp >= 6 ? 2 : 0;
-        sel = (warp & 1) ? kSel01 : kSel00;
-      }
-    }
-    {
+    const int pr = diag ? static_cast<int>((kDiagR >> (2 * warp)) & 3) : warp >> 2;
+    const int pc = diag ? static_cast<int>((kDiagC >> (2 * warp)) & 3) : warp & 3;
+    const int sel = diag ? static_cast<int>((kDiagSel >> (2 * warp)) & 3) : kSelAll;
+    if (sel != kSelIdle) {
       const int nvalid = args.T - x.c * kTC;
       const uint32_t a_base = smem_u32(sm.plane[buf][0][0]);
       const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
       const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
       const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
-      if (sel == kSelAll)
-        chunk_mma<kSelAll>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
-      else if (sel == kSel00)
-        chunk_mma<kSel00>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
-      else
-        chunk_mma<kSel01>(a_base, b01, b2, pwm, pwn, lane, ksteps, acc);
+      if (args.hybrid && ksteps == kTC / 32) {  // (a ragged last chunk's zero samples take either path)
+        if (sel == kSelAll)
+          chunk_hybrid<kSelAll>(a_base, b01, b2, pr, pc, lane, acc);
+        else if (sel == kSelN0)
+          chunk_hybrid<kSelN0>(a_base, b01, b2, pr, pc, lane, acc);
+        else
+          chunk_hybrid<kSelN1>(a_base, b01, b2, pr, pc, lane, acc);
+      } else if (sel == kSelAll) {
+        chunk_mma<kSelAll>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+      } else if (sel == kSelN0) {
+        chunk_mma<kSelN0>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+      } else {
+        chunk_mma<kSelN1>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
@@ -421,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       const int4 w = args.items[x.item];
       const bool whole = w.z == 0 && w.w == args.nch;
       const int mode = whole ? (args.fresh ? 0 : 1) : 2;
-      write_piece(args, x.f, x.bi * kTile, x.bj * kTile, pwm, pwn, lane, mode, sel, acc);
+      if (sel != kSelIdle) write_piece(args, x.f, x.bi * kTile, x.bj * kTile, pr, pc, lane, mode, sel, acc);
       zero_acc(acc);
     }
     x.next();

@@ -115,3 +115,14 @@ __device__ __forceinline__ void setmaxnreg_dec() {
   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(kRegs));
 }
 }  // namespace xe
+
+namespace xe {
+// 4-way signed int8 dot product plus int32 add on the integer ALU pipe.
+__device__ __forceinline__ void dp4a_acc(int32_t& d, uint32_t a, uint32_t b) {
+  asm volatile("dp4a.s32.s32 %0, %1, %2, %0;\n" : "+r"(d) : "r"(a), "r"(b));
+}
+
+__device__ __forceinline__ void lds64(uint32_t addr, uint32_t& w0, uint32_t& w1) {
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(w0), "=r"(w1) : "r"(addr));
+}
+}  // namespace xe

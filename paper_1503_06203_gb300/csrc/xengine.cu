@@ -76,6 +76,14 @@ int device_setup(int dev) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Product path: 1 = tensor cores + dp4a (chunk_hybrid), 0 = tensor cores only.
+// XE_PRODUCT=mma in the environment selects the tensor-core-only path.
+int product_hybrid() {
+  const char* v = getenv("XE_PRODUCT");
+  return (v && strcmp(v, "mma") == 0) ? 0 : 1;
+}
+const int g_hybrid = product_hybrid();
+
 // Upper-triangle tile order: block rows bi <= block columns bj, row-major (Fig. 1).
 void triangle_tiles(int32_t N, int32_t tile, std::vector<int32_t>& bi, std::vector<int32_t>& bj) {
   const int32_t nb = static_cast<int32_t>(ceil_div(N, tile));
@@ -284,6 +292,7 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.B = h->B;
   a.vis = h->acc;
   a.fresh = h->fresh ? 1 : 0;
+  a.hybrid = g_hybrid;
   a.err = h->d_err;
   xe::corr_tile_kernel<<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
@@ -727,6 +736,7 @@ extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int3
   a.B = static_cast<int64_t>(N) * (N + 1) / 2;
   a.vis = vis_dev;
   a.fresh = 1;
+  a.hybrid = 0;
   a.err = reinterpret_cast<int32_t*>(scratch);
   const int grid = static_cast<int>(std::min<int64_t>(slots, nitems));
   xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
