@@ -46,8 +46,19 @@ enum : int { kErrTimeoutFull = 1, kErrTimeoutEmpty = 2 };
 // Plane slots. A side (rows i): xr, xi, s = xr + xi. B side (columns j): xr, xi, d = xr - xi.
 enum : int { kPxr = 0, kPxi = 1, kPsd = 2 };
 
+// One frame of a batched launch (device memory; the TMA descriptor first, 64-byte aligned).
+struct __align__(64) FrameDesc {
+  CUtensorMap map;   // [T][F][Np] bytes of the frame
+  int32_t N, T, nch, fresh;
+  int64_t B;         // N(N+1)/2
+  int32_t* vis;      // [F][B][2] accumulators of the frame's handle
+};
+
 struct CorrArgs {
-  const int4* items;    // {band f, bi | bj << 16, first chunk, end chunk}; CTA k takes items k, k+grid, ...
+  // {band f (| frame << 20 in a batch), bi | bj << 16, first chunk, end chunk};
+  // CTA k takes items k, k + grid, ...
+  const int4* items;
+  const FrameDesc* frames = nullptr;  // batch: per-frame descriptors; nullptr: the one frame described below
   int32_t nitems;
   int32_t nch;          // chunks per tile: ceil(T / kTC)
   int32_t T;            // samples in the frame
@@ -89,7 +100,7 @@ __device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
 // store their elements in the order slot ^ 1, so that loads and stores are
 // free of bank conflicts; runtime prmt selectors undo both reorderings.
 template <bool kMasked>
-__device__ __forceinline__ void unpack_unit(const uint8_t* box, uint8_t* pl0, uint8_t* pl1, uint8_t* pl2,
+__device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, uint32_t pl1, uint32_t pl2,
                                             bool side_b, int eg, int tg, int p, int nvalid) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(box);
   uint32_t r[16];
@@ -129,9 +140,9 @@ __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint8_t* pl0, ui
       sd[j] = side_b ? (((hi | 0x80808080u) - lo) ^ 0x80808080u) : ((hi + lo + 0x70707070u) ^ 0x80808080u);
     }
     const uint32_t off = plane_off(e, tg);
-    if (pl0) *reinterpret_cast<uint4*>(pl0 + off) = make_uint4(xr[0], xr[1], xr[2], xr[3]);
-    if (pl1) *reinterpret_cast<uint4*>(pl1 + off) = make_uint4(xi[0], xi[1], xi[2], xi[3]);
-    *reinterpret_cast<uint4*>(pl2 + off) = make_uint4(sd[0], sd[1], sd[2], sd[3]);
+    if (pl0) sts128(pl0 + off, xr[0], xr[1], xr[2], xr[3]);  // (0 = plane not wanted)
+    if (pl1) sts128(pl1 + off, xi[0], xi[1], xi[2], xi[3]);
+    sts128(pl2 + off, sd[0], sd[1], sd[2], sd[3]);
   }
 }
 
@@ -241,8 +252,8 @@ __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base,
 // whose other parts other CTAs add). Entries with i > j, outside the N x N
 // matrix, or in sub-tiles the warp did not compute are dropped; entry (i, j)
 // of band f lives at (f*B + p(i,j))*2, p(i,j) = i*N - i(i-1)/2 + j - i.
-__device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, int j0, int pr, int pc, int lane,
-                                            int mode, int sel, int32_t (&acc)[3][2][4]) {
+__device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int f, int i0, int j0, int pr, int pc,
+                                            int lane, int mode, int sel, int32_t (&acc)[3][2][4]) {
   // fold in place: Re = P1 + P2 into acc[0], Im = Q - P1 + P2 into acc[2] (modulo 2^32;
   // exact for in-range Re, Im)
 #pragma unroll
@@ -254,8 +265,7 @@ __device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, in
       acc[2][ni][r] = static_cast<int32_t>(static_cast<uint32_t>(acc[2][ni][r]) - p1 + p2);
     }
   const int g = lane >> 2, q = lane & 3;
-  const int N = a.N;
-  int32_t* base = a.vis + static_cast<int64_t>(f) * a.B * 2;
+  int32_t* base = vis + static_cast<int64_t>(f) * B * 2;
   const int jw = j0 + pc * 16 + 2 * q;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
@@ -296,26 +306,43 @@ __device__ __forceinline__ void write_piece(const CorrArgs& a, int f, int i0, in
 // (three int32 accumulator sets, 24 registers a thread); four of them share
 // each SM sub-partition. Warps 16-19: unpack; lane 0 of warp 16 also issues
 // the TMA loads. One CTA per SM.
-// Walks (item, chunk) pairs of this CTA in order.
+// Walks (item, chunk) pairs of this CTA in order. T and nch are the current
+// item's frame's (from its descriptor in a batch, else from args); the writer
+// reads the rest when it needs it.
 struct Walk {
-  int item, c, f, bi, bj, c1;
+  int item, c, f, bi, bj, c1, frame, T, nch;
   const int4* items;
+  const FrameDesc* frames;
   int nitems, stride;
   __device__ __forceinline__ void load() {
     if (item < nitems) {
       const int4 w = items[item];
-      f = w.x;
       bi = w.y & 0xFFFF;
       bj = w.y >> 16;
       c = w.z;
       c1 = w.w;
+      if (frames) {
+        f = w.x & 0xFFFFF;
+        const int fr = w.x >> 20;
+        if (fr != frame) {
+          frame = fr;
+          T = frames[fr].T;
+          nch = frames[fr].nch;
+        }
+      } else {
+        f = w.x;
+      }
     }
   }
-  __device__ __forceinline__ void start(const int4* it, int n, int first, int step) {
-    items = it;
-    nitems = n;
+  __device__ __forceinline__ void start(const CorrArgs& a, int first, int step) {
+    items = a.items;
+    frames = a.frames;
+    nitems = a.nitems;
     stride = step;
     item = first;
+    frame = -1;
+    T = a.T;
+    nch = a.nch;
     load();
   }
   __device__ __forceinline__ bool valid() const { return item < nitems; }
@@ -324,6 +351,9 @@ struct Walk {
       item += stride;
       load();
     }
+  }
+  __device__ __forceinline__ const CUtensorMap* map(const CUtensorMap* single) const {
+    return frames ? &frames[frame].map : single;
   }
 };
 
@@ -353,25 +383,31 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const bool producer = uw == 0 && lane == 0;
     const int eg = lane & 15, p = lane >> 4, tg = 2 * (uw & 1) + p;
     Walk ld;  // the TMA issuer walks the same units, kStages ahead
-    ld.start(args.items, args.nitems, blockIdx.x, gridDim.x);
+    ld.start(args, blockIdx.x, gridDim.x);
     uint32_t issued = 0;
+    const CUtensorMap* fenced = nullptr;
     auto issue = [&](void) {
       const int s = issued % kStages;
       const bool diag = ld.bi == ld.bj;
+      const CUtensorMap* map = ld.map(&tmap);
+      if (args.frames && map != fenced) {  // a frame descriptor copied in before the launch
+        tensormap_acquire(map);
+        fenced = map;
+      }
       mbar_arrive_expect_tx(&sm.full[s], diag ? kBoxBytes : 2 * kBoxBytes);
-      tma_load_3d(sm.box[s][0], &tmap, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
-      if (!diag) tma_load_3d(sm.box[s][1], &tmap, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
+      tma_load_3d(sm.box[s][0], map, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
+      if (!diag) tma_load_3d(sm.box[s][1], map, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
       ++issued;
       ld.next();
     };
     if (producer) {
-      tma_prefetch_desc(&tmap);
+      if (!args.frames) tma_prefetch_desc(&tmap);
       for (int k = 0; k < kStages && ld.valid(); ++k) issue();
     }
     uint32_t it = 0;
     bool ok = true;
     Walk x;
-    for (x.start(args.items, args.nitems, blockIdx.x, gridDim.x); x.valid(); x.next(), ++it) {
+    for (x.start(args, blockIdx.x, gridDim.x); x.valid(); x.next(), ++it) {
       const bool diag = x.bi == x.bj;
       const int s = it % kStages, buf = it % kPlaneBufs;
       // the plane buffer must be free (its previous chunk's products issued) and the box landed
@@ -381,16 +417,16 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         ok = false;
         break;
       }
-      const int nvalid = args.T - x.c * kTC;
+      const int nvalid = x.T - x.c * kTC;
       const int blk = diag ? 0 : (uw >> 1);
       const uint8_t* box = sm.box[s][blk];
-      uint8_t* pl0 = sm.plane[buf][blk][kPxr];
-      uint8_t* pl1 = sm.plane[buf][blk][kPxi];
-      uint8_t* pl2 = sm.plane[buf][blk][kPsd];
+      uint32_t pl0 = smem_u32(sm.plane[buf][blk][kPxr]);
+      uint32_t pl1 = smem_u32(sm.plane[buf][blk][kPxi]);
+      uint32_t pl2 = smem_u32(sm.plane[buf][blk][kPsd]);
       bool side_b = blk == 1;
-      if (diag && uw >= 2) {  // diagonal tile: warps 6-7 make the B side's xr - xi plane
-        pl0 = pl1 = nullptr;
-        pl2 = sm.plane[buf][1][kPsd];
+      if (diag && uw >= 2) {  // diagonal tile: the last two unpack warps make the B side's xr - xi plane
+        pl0 = pl1 = 0;
+        pl2 = smem_u32(sm.plane[buf][1][kPsd]);
         side_b = true;
       }
       if (nvalid >= kTC)
@@ -429,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   zero_acc(acc);
   uint32_t it = 0;
   Walk x;
-  for (x.start(args.items, args.nitems, blockIdx.x, gridDim.x); x.valid(); ++it) {
+  for (x.start(args, blockIdx.x, gridDim.x); x.valid(); ++it) {
     const bool diag = x.bi == x.bj;
     const int buf = it % kPlaneBufs;
     if (!mbar_wait_bounded(&sm.pfull[buf], (it / kPlaneBufs) & 1, kSpinLimit)) {
@@ -440,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const int pc = diag ? static_cast<int>((kDiagC >> (2 * warp)) & 3) : warp & 3;
     const int sel = diag ? static_cast<int>((kDiagSel >> (2 * warp)) & 3) : kSelAll;
     if (sel != kSelIdle) {
-      const int nvalid = args.T - x.c * kTC;
+      const int nvalid = x.T - x.c * kTC;
       const uint32_t a_base = smem_u32(sm.plane[buf][0][0]);
       const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
       const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
@@ -464,9 +500,13 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
     if (x.c + 1 == x.c1) {  // end of the item: write it
       const int4 w = args.items[x.item];
-      const bool whole = w.z == 0 && w.w == args.nch;
-      const int mode = whole ? (args.fresh ? 0 : 1) : 2;
-      if (sel != kSelIdle) write_piece(args, x.f, x.bi * kTile, x.bj * kTile, pr, pc, lane, mode, sel, acc);
+      const bool whole = w.z == 0 && w.w == x.nch;
+      const FrameDesc* d = args.frames ? &args.frames[x.frame] : nullptr;
+      const int fresh = d ? d->fresh : args.fresh;
+      const int mode = whole ? (fresh ? 0 : 1) : 2;
+      if (sel != kSelIdle)
+        write_piece(d ? d->N : args.N, d ? d->B : args.B, d ? d->vis : args.vis, x.f, x.bi * kTile, x.bj * kTile, pr,
+                    pc, lane, mode, sel, acc);
       zero_acc(acc);
     }
     x.next();

@@ -126,3 +126,18 @@ __device__ __forceinline__ void lds64(uint32_t addr, uint32_t& w0, uint32_t& w1)
   asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];\n" : "=r"(w0), "=r"(w1) : "r"(addr));
 }
 }  // namespace xe
+
+namespace xe {
+// Order the async (tensor-map) proxy's reads of a descriptor in global memory
+// after the writes that put it there.
+__device__ __forceinline__ void tensormap_acquire(const void* desc) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(reinterpret_cast<uint64_t>(desc))
+               : "memory");
+}
+}  // namespace xe
+
+namespace xe {
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+}  // namespace xe

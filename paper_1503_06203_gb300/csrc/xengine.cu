@@ -390,6 +390,235 @@ int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t s
 
 }  // namespace
 
+// ---- batched launch: many frames, one persistent kernel, replayed as a CUDA graph ----
+//
+// The frames' tiles form one work list (Sec. II.C: tiles are independent;
+// Sec. I: bands are independent). Items are whole tiles, sorted by cost
+// (longest integration first, a stable sort so one band's tiles stay
+// together) and laid out in snake order over the CTAs, so each CTA gets a
+// near-equal share. A graph of {descriptor copy, item copy, kernel} is built
+// for a batch's sizes and replayed while the sizes repeat; the copies read
+// pinned host buffers, so each replay carries the new frames. Two buffer sets
+// alternate, so a batch can be prepared while the previous one runs.
+namespace {
+
+constexpr int kMaxBatchFrames = 2047;  // frame index lives in bits 20..30 of an item
+
+struct BatchSet {
+  xe::FrameDesc* h_desc = nullptr;  // pinned
+  int4* h_items = nullptr;          // pinned
+  xe::FrameDesc* d_desc = nullptr;
+  int4* d_items = nullptr;
+  size_t cap_frames = 0, cap_items = 0;
+  cudaEvent_t done = nullptr;  // after the last graph launch that read this set
+  bool pending = false;
+  cudaGraphExec_t exec = nullptr;
+  int64_t key_frames = -1, key_items = -1, key_grid = -1, key_hybrid = -1;
+  int32_t* key_err = nullptr;
+};
+
+struct BatchCtx {
+  BatchSet set[2];
+  int next = 0;
+};
+
+std::mutex g_batch_mu;
+BatchCtx* g_batch[64];
+
+void free_set(BatchSet& b) {
+  if (b.pending && b.done) cudaEventSynchronize(b.done);
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  if (b.h_desc) cudaFreeHost(b.h_desc);
+  if (b.h_items) cudaFreeHost(b.h_items);
+  if (b.d_desc) cudaFree(b.d_desc);
+  if (b.d_items) cudaFree(b.d_items);
+  b = BatchSet();
+}
+
+int grow_set(BatchSet& b, size_t frames, size_t items) {
+  if (frames > b.cap_frames) {
+    if (b.h_desc) cudaFreeHost(b.h_desc);
+    if (b.d_desc) cudaFree(b.d_desc);
+    b.h_desc = nullptr;
+    b.d_desc = nullptr;
+    const size_t cap = std::max<size_t>(frames, 64);
+    if (cudaMallocHost(&b.h_desc, cap * sizeof(xe::FrameDesc)) != cudaSuccess ||
+        cudaMalloc(&b.d_desc, cap * sizeof(xe::FrameDesc)) != cudaSuccess)
+      return fail(CORR_ENOMEM, "batch descriptor buffers (%zu frames)", cap);
+    b.cap_frames = cap;
+    if (b.exec) {
+      cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    }
+  }
+  if (items > b.cap_items) {
+    if (b.h_items) cudaFreeHost(b.h_items);
+    if (b.d_items) cudaFree(b.d_items);
+    b.h_items = nullptr;
+    b.d_items = nullptr;
+    const size_t cap = std::max<size_t>(items + items / 4, 4096);
+    if (cudaMallocHost(&b.h_items, cap * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&b.d_items, cap * sizeof(int4)) != cudaSuccess)
+      return fail(CORR_ENOMEM, "batch work-list buffers (%zu items)", cap);
+    b.cap_items = cap;
+    if (b.exec) {
+      cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    }
+  }
+  if (!b.done && cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess)
+    return fail(CORR_ECUDA, "batch event");
+  return CORR_OK;
+}
+
+int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err) {
+  if (b.exec) {
+    cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphCreate: %s", cudaGetErrorString(e));
+  cudaGraphNode_t cp[2], kn;
+  e = cudaGraphAddMemcpyNode1D(&cp[0], g, nullptr, 0, b.d_desc, b.h_desc, nframes * sizeof(xe::FrameDesc),
+                               cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaGraphAddMemcpyNode1D(&cp[1], g, nullptr, 0, b.d_items, b.h_items, nitems * sizeof(int4),
+                                 cudaMemcpyHostToDevice);
+  CUtensorMap unused;  // batch frames carry their own descriptors
+  memset(&unused, 0, sizeof unused);
+  xe::CorrArgs a;
+  a.items = b.d_items;
+  a.frames = b.d_desc;
+  a.nitems = static_cast<int32_t>(nitems);
+  a.nch = 0;
+  a.T = 0;
+  a.N = 0;
+  a.B = 0;
+  a.vis = nullptr;
+  a.fresh = 0;
+  a.hybrid = g_hybrid;
+  a.err = err;
+  void* params[2] = {&unused, &a};
+  cudaKernelNodeParams kp;
+  memset(&kp, 0, sizeof kp);
+  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel);
+  kp.gridDim = dim3(static_cast<unsigned>(grid));
+  kp.blockDim = dim3(xe::kThreads);
+  kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
+  kp.kernelParams = params;
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&kn, g, cp, 2, &kp);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b.exec = nullptr;
+    return fail(CORR_ECUDA, "building the batch graph: %s", cudaGetErrorString(e));
+  }
+  b.key_frames = nframes;
+  b.key_items = nitems;
+  b.key_grid = grid;
+  b.key_hybrid = g_hybrid;
+  b.key_err = err;
+  return CORR_OK;
+}
+
+int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!hs || !inputs))) return fail(CORR_EINVAL, "bad batch arguments");
+  if (n == 0) return CORR_OK;
+  if (n > kMaxBatchFrames) return fail(CORR_EINVAL, "batch of %d frames exceeds %d", n, kMaxBatchFrames);
+  const int dev = hs[0] ? hs[0]->device : 0;
+  for (int k = 0; k < n; ++k) {
+    int rc = check_handle(hs[k]);
+    if (rc) return rc;
+    if (!inputs[k]) return fail(CORR_EINVAL, "batch input %d is NULL", k);
+    if (hs[k]->device != dev) return fail(CORR_EINVAL, "batch handles live on different devices");
+    if (hs[k]->F >= (1 << 20)) return fail(CORR_EINVAL, "batch frames need F < 2^20");
+    if (hs[k]->samples + hs[k]->T > CORR_MAX_SAMPLES)
+      return fail(CORR_EOVERFLOW, "batch frame %d would exceed %d samples since its handle's reset", k,
+                  CORR_MAX_SAMPLES);
+    for (int j = 0; j < k; ++j)
+      if (hs[j] == hs[k]) return fail(CORR_EINVAL, "batch handles must be distinct (frames %d and %d)", j, k);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // work list: whole tiles of every frame, costed by their integration length
+  struct It {
+    int4 w;
+    double cost;
+  };
+  std::vector<It> work;
+  for (int k = 0; k < n; ++k) {
+    std::vector<int32_t> bi, bj;
+    triangle_tiles(hs[k]->N, xe::kTile, bi, bj);
+    const int32_t nch = static_cast<int32_t>(ceil_div(hs[k]->T, xe::kTC));
+    for (int32_t f = 0; f < hs[k]->F; ++f)
+      for (size_t u = 0; u < bi.size(); ++u)
+        work.push_back({make_int4(f | (k << 20), bi[u] | (bj[u] << 16), 0, nch),
+                        (bi[u] == bj[u] ? kDiagCost : 1.0) * nch});
+  }
+  std::stable_sort(work.begin(), work.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+  const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
+  const int64_t nitems = static_cast<int64_t>(work.size());
+  const int64_t grid = std::min<int64_t>(slots, nitems);
+  if (nitems > INT32_MAX) return fail(CORR_EINVAL, "batch work list too long");
+
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (!g_batch[dev]) g_batch[dev] = new (std::nothrow) BatchCtx;
+  if (!g_batch[dev]) return fail(CORR_ENOMEM, "batch context");
+  BatchCtx& ctx = *g_batch[dev];
+  BatchSet& b = ctx.set[ctx.next];
+  if (b.pending) {  // the graph launch that last read these pinned buffers must be done
+    cudaError_t e = cudaEventSynchronize(b.done);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "waiting for a previous batch: %s", cudaGetErrorString(e));
+    b.pending = false;
+  }
+  int rc = grow_set(b, static_cast<size_t>(n), static_cast<size_t>(nitems));
+  if (rc) return rc;
+  // snake layout: position r*grid + c is CTA c's r-th item; row r runs forward or backward
+  for (int64_t i = 0; i < nitems; ++i) {
+    const int64_t r = i / grid, c = i % grid;
+    const int64_t col = (r & 1) ? grid - 1 - c : c;
+    const int64_t pos = r * grid + col;
+    b.h_items[pos < nitems ? pos : i] = work[i].w;
+  }
+  // with a ragged last row the snake's backward row may point past the end: redo it in order
+  if (nitems % grid != 0 && ((nitems / grid) & 1)) {
+    const int64_t r = nitems / grid;
+    for (int64_t i = r * grid; i < nitems; ++i) b.h_items[i] = work[i].w;
+  }
+  for (int k = 0; k < n; ++k) {
+    corr_handle* h = hs[k];
+    if ((rc = order_after_last(h, st))) return rc;
+    const uint8_t* frame;
+    int32_t np;
+    if ((rc = stage_if_needed(h, inputs[k], h->T, st, &frame, &np))) return rc;
+    xe::FrameDesc& d = b.h_desc[k];
+    if ((rc = make_tmap(&d.map, frame, np, h->F, h->T))) return rc;
+    d.N = h->N;
+    d.T = h->T;
+    d.nch = static_cast<int32_t>(ceil_div(h->T, xe::kTC));
+    d.fresh = h->fresh ? 1 : 0;
+    d.B = h->B;
+    d.vis = h->acc;
+  }
+  if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != g_hybrid ||
+      b.key_err != hs[0]->d_err)
+    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err))) return rc;
+  cudaError_t e = cudaGraphLaunch(b.exec, st);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
+  b.pending = true;
+  ctx.next ^= 1;
+  for (int k = 0; k < n; ++k) {
+    hs[k]->fresh = false;
+    hs[k]->samples += hs[k]->T;
+    ++hs[k]->launches;  // the handle's frame ran in one (shared) launch
+    if ((rc = record_last(hs[k], st))) return rc;
+  }
+  return CORR_OK;
+}
+
+}  // namespace
+
 // =================================== C ABI ===================================
 extern "C" {
 
@@ -516,12 +745,7 @@ int corr_reset(corr_handle_t* h, void* stream) {
 }
 
 int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream) {
-  if (n < 0 || (n > 0 && (!hs || !inputs))) return fail(CORR_EINVAL, "bad batch arguments");
-  for (int k = 0; k < n; ++k) {
-    int rc = corr_accumulate(hs[k], inputs[k], stream);
-    if (rc) return rc;
-  }
-  return CORR_OK;
+  return batch_impl(hs, inputs, n, stream);
 }
 
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms) {

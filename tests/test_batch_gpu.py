@@ -1,0 +1,119 @@
+"""Batched uneven frames in one persistent launch (replayed as a CUDA graph) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xe():
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    return xe
+
+
+def small_batch(count, seed, tmax=1024):
+    """The uneven-frame recipe with T capped so the oracle stays fast."""
+    out = []
+    for fr in synth.batched_frames(count, seed):
+        T = min(fr.T, tmax)
+        N = min(fr.N, 512)
+        F = min(fr.F, 8)
+        out.append(synth.Frame(N, F, T, "gauss", fr.sigma, fr.seed))
+    return out
+
+
+def run_batch(xe, frames, cors=None, reps=1):
+    import torch
+    cors = cors or [xe.Correlator(f.N, f.F, f.T) for f in frames]
+    xs = [f.make() for f in frames]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    for _ in range(reps):
+        xe.accumulate_batch(cors, xd)
+    outs = [c.readout().cpu().numpy() for c in cors]
+    torch.cuda.synchronize()
+    return cors, xs, outs
+
+
+def test_batch_matches_oracle(xe):
+    frames = small_batch(12, 1003)
+    _, xs, outs = run_batch(xe, frames)
+    for x, V in zip(xs, outs):
+        assert np.array_equal(V.astype(np.int64), oracle.visibilities(x))
+
+
+def test_batch_graph_replay_and_rebuild(xe):
+    """Same sizes twice (graph replay with new frames), then new sizes (rebuild); results add up."""
+    import torch
+    frames = small_batch(5, 77)
+    cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
+    xs1 = [f.make() for f in frames]
+    xs2 = [synth.gauss(f.N, f.F, f.T, 2.0, f.seed + 99) for f in frames]
+    xe.accumulate_batch(cors, [torch.from_numpy(x).cuda() for x in xs1])
+    xe.accumulate_batch(cors, [torch.from_numpy(x).cuda() for x in xs2])
+    for c, a, b in zip(cors, xs1, xs2):
+        assert np.array_equal(c.readout(reset=True).cpu().numpy().astype(np.int64),
+                              oracle.visibilities(a) + oracle.visibilities(b))
+    # a different batch (fewer frames, other sizes) rebuilds the graph
+    sub = cors[1:4]
+    xs3 = [synth.gauss(c.N, c.F, c.T, 3.0, 5 + k) for k, c in enumerate(sub)]
+    xe.accumulate_batch(sub, [torch.from_numpy(x).cuda() for x in xs3])
+    for c, x in zip(sub, xs3):
+        assert np.array_equal(c.readout().cpu().numpy().astype(np.int64), oracle.visibilities(x))
+    torch.cuda.synchronize()
+
+
+def test_batch_rejects_duplicates_and_overflow(xe):
+    import torch
+    c = xe.Correlator(64, 1, 256)
+    x = torch.zeros((256, 1, 64), dtype=torch.uint8, device="cuda")
+    with pytest.raises(xe.XEngineError):
+        xe.accumulate_batch([c, c], [x, x])
+    T = 8 * 1024 * 1024
+    big = xe.Correlator(16, 1, T)
+    xb = torch.zeros((T, 1, 16), dtype=torch.uint8, device="cuda")
+    xe.accumulate_batch([big], [xb])
+    with pytest.raises(xe.XEngineError) as ei:  # 2 * 2^23 = 16777216 > 16777215
+        xe.accumulate_batch([big], [xb])
+    assert ei.value.code == -4
+    assert big.samples == T
+    V = big.readout().cpu().numpy()
+    assert (V[0, :, 0] == 128 * T).all() and not V[0, :, 1].any()
+
+
+@pytest.mark.slow
+def test_full_uneven_batch_sampled_and_freivalds(xe):
+    """All 64 frames of the uneven-frame workload in one launch: sampled entries, autos, Freivalds per frame."""
+    import torch
+    frames = synth.batched_frames()
+    cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
+    xs = [f.make() for f in frames]
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    xe.accumulate_batch(cors, xd)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    for k, (fr, c, x) in enumerate(zip(frames, cors, xs)):
+        V = c.readout().cpu().numpy()
+        K = 300
+        f = rng.integers(0, fr.F, K)
+        i = rng.integers(0, fr.N, K)
+        j = rng.integers(0, fr.N, K)
+        i, j = np.minimum(i, j), np.maximum(i, j)
+        assert np.array_equal(V[f, xe.packed_index(fr.N, i, j)].astype(np.int64),
+                              oracle.entries(x, np.stack([f, i, j], 1))), k
+        w = rng.integers(-3, 4, size=(fr.F, fr.N, 2)).astype(np.int64)
+        rhs = oracle.freivalds_rhs(x, w)
+        iu, ju = np.triu_indices(fr.N)
+        for b in range(fr.F):
+            wc = w[b, :, 0] + 1j * w[b, :, 1]
+            Vc = V[b, :, 0].astype(np.float64) + 1j * V[b, :, 1].astype(np.float64)
+            t1 = Vc * wc[ju]
+            off = iu != ju
+            t2 = np.conj(Vc[off]) * wc[iu[off]]
+            lr = np.bincount(iu, weights=t1.real, minlength=fr.N) + np.bincount(ju[off], weights=t2.real, minlength=fr.N)
+            li = np.bincount(iu, weights=t1.imag, minlength=fr.N) + np.bincount(ju[off], weights=t2.imag, minlength=fr.N)
+            assert np.array_equal(np.rint(lr).astype(np.int64), rhs[b, :, 0]), (k, b)
+            assert np.array_equal(np.rint(li).astype(np.int64), rhs[b, :, 1]), (k, b)
