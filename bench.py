@@ -38,6 +38,7 @@ WORKLOADS = {
     "pathfinder": ("PATHFINDER", "Pathfinder shape N=256 F=256 T=16384, Gaussian sigma=2.5 levels, one frame per launch"),
     "large_n": ("LARGE_N", "large N: N=8192 F=4 T=2048, sigma=2.5 plus a common tone, one frame per launch"),
 }
+EXTRA_WORKLOADS = ("batched", "served")
 KERNEL_NAME = "corr_tile_kernel"
 KERNEL_SOURCES = ["paper_1503_06203_gb300/csrc/xe_corr.cuh", "paper_1503_06203_gb300/csrc/xe_ptx.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "corr_tile_kernel_pathfinder_traffic.md")
@@ -50,7 +51,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["xengine", "reference"], default="xengine")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="pathfinder")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(EXTRA_WORKLOADS), default="pathfinder")
+    ap.add_argument("--rates", default="10,25,40", help="served: Poisson arrival rates (frames/s) to sweep")
+    ap.add_argument("--served-frames", type=int, default=160, help="served: frames per rate")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -380,9 +383,100 @@ def run_xengine(args, wl_key):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batched / served
+def run_batched(args):
+    """64 uneven frames: one launch per frame vs one batched (graph-replayed) launch per step."""
+    import torch
+
+    import paper_1503_06203_gb300 as xe
+    import synth
+    xe.build()
+    frames = synth.batched_frames()
+    cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
+    xs = [torch.from_numpy(f.make()).cuda() for f in frames]
+    ops = sum(4.0 * f.N * (f.N + 1) * f.F * f.T for f in frames)
+    stream = torch.cuda.current_stream()
+
+    def step(batched):
+        for c in cors:
+            c.reset()
+        if batched:
+            xe.accumulate_batch(cors, xs)
+        else:
+            for c, x in zip(cors, xs):
+                c.accumulate(x)
+
+    res = {}
+    for mode in (False, True):
+        for _ in range(args.warmup):
+            step(mode)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res["batched" if mode else "plain"] = {"ms_per_step": round(ms, 4), "frames_per_s": round(len(frames) / ms * 1e3, 2),
+                                               "effective_tops": round(ops / ms / 1e9, 3),
+                                               "launches_per_step": 1 if mode else len(frames)}
+    line = {"metric": "Effective TOPS", "value": res["batched"]["effective_tops"], "unit": "TOPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "s8 x s8 -> s32",
+            "data": "synthetic (seeded generator, paper's shapes)",
+            "config": {"workload": "64 uneven frames (N 64..2048, F 1..64, T 512..8192, sigma 1.5..3.5) per step",
+                       "frames": len(frames), "effective_ops_per_step": ops},
+            "batched": res["batched"], "plain": res["plain"],
+            "speedup_batched_over_plain": round(res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"], 3)}
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    """32 served streams with Poisson arrivals: continuous batching vs one frame per launch."""
+    import numpy as np
+    import torch
+
+    import paper_1503_06203_gb300 as xe
+    import synth
+    from paper_1503_06203_gb300 import serve
+    xe.build()
+    rng = np.random.default_rng(1004)
+    specs = [serve.StreamSpec(int(rng.choice([256, 1024, 2048])), int(rng.choice([16, 64, 256]))) for _ in range(32)]
+    t_min, t_max = 1024, 8192
+    pool_bytes = max(s.N * s.F for s in specs) * t_max
+    pool = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory()
+    synth.gauss(pool_bytes, 1, 1, 2.5, 1004, out=pool.numpy().reshape(1, 1, -1))
+    budget = 24 << 30
+    srv = serve.Server(specs, t_max, pool, budget_bytes=budget, readout_every=16)
+    sweeps = []
+    for k, rate in enumerate(float(r) for r in args.rates.split(",")):
+        arr = serve.poisson_arrivals(rate, args.served_frames, len(specs), t_min, t_max, pool_bytes, specs, 1004 + k)
+        out = {"rate_hz": rate}
+        for mode in ("served", "plain"):
+            srv.reset()
+            st = srv.run_served(arr) if mode == "served" else srv.run_plain(arr)
+            out[mode] = st.summary()
+        sweeps.append(out)
+    best = max(sweeps, key=lambda d: d["served"]["frames_per_s"])
+    acc_gb = sum(s.F * s.N * (s.N + 1) * 4 for s in specs) / 1e9
+    line = {"metric": "served frames/s and p50/p99 frame latency (continuous batching vs one frame per launch)",
+            "value": best["served"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "s8 x s8 -> s32", "data": "synthetic (seeded generator, paper's shapes)",
+            "config": {"workload": "32 streams, N in {256,1024,2048}, F in {16,64,256} per stream, T 1024..8192 "
+                                   "per frame, Poisson arrivals, readout every 16 frames",
+                       "streams": [[s.N, s.F] for s in specs], "resident_accumulators_gb": round(acc_gb, 2),
+                       "input_budget_gb": budget / 2 ** 30, "frames_per_rate": args.served_frames},
+            "sweep": sweeps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
+    elif args.impl == "reference":
         run_reference(args, args.workload)
     else:
         run_xengine(args, args.workload)

@@ -120,6 +120,15 @@ int corr_reset(corr_handle_t* h, void* stream);
  */
 int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream);
 
+/*
+ * corr_accumulate_batch_ex -- as corr_accumulate_batch, with frame k holding
+ * Ts[k] samples (host array; 1 <= Ts[k]; NULL = each handle's T). Lets a
+ * stream of frames of varying length share one handle's resident
+ * accumulators (the sample cap counts the samples actually added).
+ */
+int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
+                             void* stream);
+
 /* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit). */
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms);
 

@@ -179,11 +179,17 @@ def correlate_noalloc(x, out, status=None, stream=None):
 
 
 def accumulate_batch(correlators, inputs, stream=None):
-    """One call for several frames: inputs[k] (device uint8 tensor) is added to correlators[k]."""
+    """One launch for several frames: inputs[k] (device uint8 [T_k][F][N]) is added to correlators[k].
+
+    T_k may differ from the correlator's T (frames of varying length); the
+    correlators must be distinct.
+    """
     n = len(correlators)
     assert len(inputs) == n
     for c, x in zip(correlators, inputs):
-        c._check_frame(x)
+        if tuple(x.shape[1:]) != (c.F, c.N) or not x.is_contiguous():
+            raise ValueError(f"frame shape {tuple(x.shape)} does not fit (T, F, N) with F={c.F}, N={c.N}")
     hs = (ctypes.c_void_p * n)(*[c._h.value for c in correlators])
     xs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in inputs])
-    check(lib().corr_accumulate_batch(hs, xs, n, _stream_ptr(stream)))
+    Ts = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in inputs])
+    check(lib().corr_accumulate_batch_ex(hs, xs, Ts, n, _stream_ptr(stream)))

@@ -28,6 +28,7 @@ SIGNATURES = [
     ("corr_readout_host", _int, [_vp, _vp, _int, _vp]),
     ("corr_reset", _int, [_vp, _vp]),
     ("corr_accumulate_batch", _int, [_vp, _vp, _int, _vp]),
+    ("corr_accumulate_batch_ex", _int, [_vp, _vp, _vp, _int, _vp]),
     ("corr_synchronize", _int, [_vp, _i64]),
     ("corr_status", _int, [_vp]),
     ("corr_samples", _i64, [_vp]),

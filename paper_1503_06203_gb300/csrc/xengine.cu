@@ -522,7 +522,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   return CORR_OK;
 }
 
-int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream) {
+int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n, void* stream) {
   if (n < 0 || (n > 0 && (!hs || !inputs))) return fail(CORR_EINVAL, "bad batch arguments");
   if (n == 0) return CORR_OK;
   if (n > kMaxBatchFrames) return fail(CORR_EINVAL, "batch of %d frames exceeds %d", n, kMaxBatchFrames);
@@ -533,7 +533,9 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, vo
     if (!inputs[k]) return fail(CORR_EINVAL, "batch input %d is NULL", k);
     if (hs[k]->device != dev) return fail(CORR_EINVAL, "batch handles live on different devices");
     if (hs[k]->F >= (1 << 20)) return fail(CORR_EINVAL, "batch frames need F < 2^20");
-    if (hs[k]->samples + hs[k]->T > CORR_MAX_SAMPLES)
+    const int32_t Tk = Ts ? Ts[k] : hs[k]->T;
+    if (Tk < 1 || Tk > CORR_MAX_SAMPLES) return fail(CORR_EINVAL, "batch frame %d: T=%d out of range", k, Tk);
+    if (hs[k]->samples + Tk > CORR_MAX_SAMPLES)
       return fail(CORR_EOVERFLOW, "batch frame %d would exceed %d samples since its handle's reset", k,
                   CORR_MAX_SAMPLES);
     for (int j = 0; j < k; ++j)
@@ -549,7 +551,7 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, vo
   for (int k = 0; k < n; ++k) {
     std::vector<int32_t> bi, bj;
     triangle_tiles(hs[k]->N, xe::kTile, bi, bj);
-    const int32_t nch = static_cast<int32_t>(ceil_div(hs[k]->T, xe::kTC));
+    const int32_t nch = static_cast<int32_t>(ceil_div(Ts ? Ts[k] : hs[k]->T, xe::kTC));
     for (int32_t f = 0; f < hs[k]->F; ++f)
       for (size_t u = 0; u < bi.size(); ++u)
         work.push_back({make_int4(f | (k << 20), bi[u] | (bj[u] << 16), 0, nch),
@@ -587,15 +589,16 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, vo
   }
   for (int k = 0; k < n; ++k) {
     corr_handle* h = hs[k];
+    const int32_t Tk = Ts ? Ts[k] : h->T;
     if ((rc = order_after_last(h, st))) return rc;
     const uint8_t* frame;
     int32_t np;
-    if ((rc = stage_if_needed(h, inputs[k], h->T, st, &frame, &np))) return rc;
+    if ((rc = stage_if_needed(h, inputs[k], Tk, st, &frame, &np))) return rc;
     xe::FrameDesc& d = b.h_desc[k];
-    if ((rc = make_tmap(&d.map, frame, np, h->F, h->T))) return rc;
+    if ((rc = make_tmap(&d.map, frame, np, h->F, Tk))) return rc;
     d.N = h->N;
-    d.T = h->T;
-    d.nch = static_cast<int32_t>(ceil_div(h->T, xe::kTC));
+    d.T = Tk;
+    d.nch = static_cast<int32_t>(ceil_div(Tk, xe::kTC));
     d.fresh = h->fresh ? 1 : 0;
     d.B = h->B;
     d.vis = h->acc;
@@ -610,7 +613,7 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, vo
   ctx.next ^= 1;
   for (int k = 0; k < n; ++k) {
     hs[k]->fresh = false;
-    hs[k]->samples += hs[k]->T;
+    hs[k]->samples += Ts ? Ts[k] : hs[k]->T;
     ++hs[k]->launches;  // the handle's frame ran in one (shared) launch
     if ((rc = record_last(hs[k], st))) return rc;
   }
@@ -745,7 +748,12 @@ int corr_reset(corr_handle_t* h, void* stream) {
 }
 
 int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream) {
-  return batch_impl(hs, inputs, n, stream);
+  return batch_impl(hs, inputs, nullptr, n, stream);
+}
+
+int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
+                             void* stream) {
+  return batch_impl(hs, inputs, Ts, n, stream);
 }
 
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms) {

@@ -1,0 +1,274 @@
+"""Served correlation streams: continuous batching over the C ABI.
+
+A correlation stream is one instrument's data flow: N elements and F bands,
+fixed for the stream, arriving as frames of T samples (Sec. III: time
+steps of all bands of all elements). Each stream keeps its int32
+visibilities resident on the device (one Correlator handle) and reads them
+out every `readout_every` frames, which starts the next integration
+(Sec. II.A: products are accumulated over many samples).
+
+The server admits arriving frames while their input bytes fit a device-
+memory budget (a ring inside one preallocated slab), copies each admitted
+frame to the device on a copy stream, and launches every copied frame not
+yet correlated in one batched launch (at most one frame per stream per
+launch: a stream's frames add into the same accumulators in arrival
+order). Frames keep arriving and copying while launches run; up to two
+launches are in flight. The plain mode is the reference: one frame per
+launch, each waited for before the next starts.
+
+PyTorch provides device memory, pinned host memory and streams; every
+correlation runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Correlator, accumulate_batch, baselines
+
+import torch
+
+
+@dataclass
+class StreamSpec:
+    N: int
+    F: int
+
+
+@dataclass
+class Arrival:
+    t: float          # seconds after the start of the run
+    stream: int
+    T: int
+    offset: int       # byte offset of the frame's data in the host pool
+
+
+@dataclass
+class FrameRecord:
+    arrival: float
+    done: float = float("nan")
+
+
+@dataclass
+class RunStats:
+    mode: str
+    frames: int
+    seconds: float
+    latencies_ms: list = field(default_factory=list)
+    ops: float = 0.0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms)
+        return {"mode": self.mode, "frames": self.frames, "seconds": round(self.seconds, 4),
+                "frames_per_s": round(self.frames / self.seconds, 3),
+                "effective_tops": round(self.ops / self.seconds / 1e12, 3),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat.size else None,
+                "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat.size else None}
+
+
+def poisson_arrivals(rate_hz: float, count: int, streams: int, t_min: int, t_max: int, pool_bytes: int,
+                     specs, seed: int) -> list[Arrival]:
+    """Poisson arrivals at `rate_hz`; stream uniform; T uniform in [t_min, t_max], a multiple of 256."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, count))
+    out = []
+    for k in range(count):
+        s = int(rng.integers(0, streams))
+        T = 256 * int(rng.integers(t_min // 256, t_max // 256 + 1))
+        nbytes = T * specs[s].F * specs[s].N
+        off = int(rng.integers(0, max(1, (pool_bytes - nbytes) // 256 + 1))) * 256
+        out.append(Arrival(float(t[k]), s, T, off))
+    return out
+
+
+class RingSlab:
+    """First-in-first-out allocator inside one device buffer: the in-flight input budget.
+
+    The live region is one circular span [tail, head). A frame may finish
+    before frames admitted earlier (a stream's next frame waits for the
+    stream's current one); its space is marked free and reclaimed once every
+    older frame is done too.
+    """
+
+    def __init__(self, nbytes: int, device: str | None = "cuda"):
+        # device=None keeps only the bookkeeping (host-side tests)
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device) if device else None
+        self.size = nbytes
+        self.head = 0
+        self.live = collections.deque()  # [start, end, freed], oldest first
+        self.used = 0
+
+    def alloc(self, nbytes: int):
+        nbytes = (nbytes + 255) // 256 * 256
+        if nbytes > self.size:
+            raise ValueError("frame larger than the device-memory budget")
+        if not self.live:
+            start = 0
+        else:
+            tail = self.live[0][0]
+            if self.head > tail:  # free: [head, size) and [0, tail)
+                if self.head + nbytes <= self.size:
+                    start = self.head
+                elif nbytes <= tail:
+                    start = 0
+                else:
+                    return None
+            elif self.head + nbytes <= tail:  # wrapped: free [head, tail)
+                start = self.head
+            else:
+                return None
+        self.live.append([start, start + nbytes, False])
+        self.head = start + nbytes
+        self.used += nbytes
+        return start
+
+    def free(self, start: int):
+        for entry in self.live:
+            if entry[0] == start and not entry[2]:
+                entry[2] = True
+                break
+        else:
+            raise KeyError(start)
+        while self.live and self.live[0][2]:
+            s, e, _ = self.live.popleft()
+            self.used -= e - s
+        if not self.live:
+            self.head = 0
+
+
+class Server:
+    """Streams with resident accumulators, served by continuous batching or one frame per launch."""
+
+    def __init__(self, specs: list[StreamSpec], t_max: int, pool: torch.Tensor, budget_bytes: int,
+                 readout_every: int = 16):
+        self.specs = specs
+        self.t_max = t_max
+        self.pool = pool  # pinned host bytes the frames are cut from
+        self.readout_every = readout_every
+        self.cors = [Correlator(s.N, s.F, t_max) for s in specs]
+        self.outs = [torch.empty((s.F, baselines(s.N), 2), dtype=torch.int32, device="cuda") for s in specs]
+        self.readouts = [[] for _ in specs]  # host copies of every readout (for checks), optional
+        self.keep_readouts = False
+        self.counts = [0] * len(specs)
+        self.ring = RingSlab(budget_bytes)
+        self.copy_stream = torch.cuda.Stream()
+        self.compute_stream = torch.cuda.Stream()
+
+    def _frame_view(self, a: Arrival) -> torch.Tensor:
+        s = self.specs[a.stream]
+        n = a.T * s.F * s.N
+        return self.pool[a.offset:a.offset + n].view(a.T, s.F, s.N)
+
+    def _after_frame(self, stream_id: int):
+        """Readout every `readout_every` frames of a stream (on the compute stream)."""
+        self.counts[stream_id] += 1
+        if self.counts[stream_id] % self.readout_every == 0:
+            self.cors[stream_id].readout(self.outs[stream_id], reset=True, stream=self.compute_stream)
+            if self.keep_readouts:  # (a synchronous copy after the readout, for checks only)
+                with torch.cuda.stream(self.compute_stream):
+                    self.readouts[stream_id].append(self.outs[stream_id].cpu())
+
+    def reset(self):
+        for c in self.cors:
+            c.reset()
+        self.counts = [0] * len(self.specs)
+        self.readouts = [[] for _ in self.specs]
+
+    def ops(self, arrivals) -> float:
+        return sum(4.0 * self.specs[a.stream].N * (self.specs[a.stream].N + 1) * self.specs[a.stream].F * a.T
+                   for a in arrivals)
+
+    # ---------------------------------------------------------------- served
+    def run_served(self, arrivals: list[Arrival], max_inflight: int = 2) -> RunStats:
+        recs = [FrameRecord(a.t) for a in arrivals]
+        pending = collections.deque(range(len(arrivals)))  # not yet arrived
+        waiting = collections.deque()   # arrived, waiting for budget
+        copying = collections.deque()   # (idx, slab offset, copy event)
+        ready = []                      # copied, not launched: (idx, offset)
+        inflight = collections.deque()  # (done event, [(idx, offset)])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        done = 0
+        while done < len(arrivals):
+            now = time.perf_counter() - t0
+            while pending and arrivals[pending[0]].t <= now:
+                waiting.append(pending.popleft())
+            # admission by the device-memory budget, in arrival order
+            while waiting:
+                k = waiting[0]
+                a = arrivals[k]
+                s = self.specs[a.stream]
+                off = self.ring.alloc(a.T * s.F * s.N)
+                if off is None:
+                    break
+                waiting.popleft()
+                src = self._frame_view(a)
+                dst = self.ring.buf[off:off + src.numel()]
+                with torch.cuda.stream(self.copy_stream):
+                    dst.copy_(src.view(-1), non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(self.copy_stream)
+                copying.append((k, off, ev))
+            while copying and copying[0][2].query():
+                k, off, _ = copying.popleft()
+                ready.append((k, off))
+            # one launch over every copied frame, one frame per stream (oldest first)
+            if ready and len(inflight) < max_inflight:
+                chosen, seen, rest = [], set(), []
+                for k, off in ready:
+                    sid = arrivals[k].stream
+                    if sid in seen:
+                        rest.append((k, off))
+                    else:
+                        seen.add(sid)
+                        chosen.append((k, off))
+                ready = rest
+                cors, xs = [], []
+                for k, off in chosen:
+                    a = arrivals[k]
+                    s = self.specs[a.stream]
+                    cors.append(self.cors[a.stream])
+                    xs.append(self.ring.buf[off:off + a.T * s.F * s.N].view(a.T, s.F, s.N))
+                accumulate_batch(cors, xs, stream=self.compute_stream)
+                for k, _ in chosen:
+                    self._after_frame(arrivals[k].stream)
+                ev = torch.cuda.Event()
+                ev.record(self.compute_stream)
+                inflight.append((ev, chosen))
+            while inflight and inflight[0][0].query():
+                _, chosen = inflight.popleft()
+                t = time.perf_counter() - t0
+                for k, off in chosen:
+                    recs[k].done = t
+                    self.ring.free(off)
+                    done += 1
+            if not (inflight and inflight[0][0].query()) and not copying and not ready:
+                time.sleep(20e-6)
+        seconds = time.perf_counter() - t0 - arrivals[0].t
+        st = RunStats("served", len(arrivals), seconds, [1e3 * (r.done - a.t) for r, a in zip(recs, arrivals)],
+                      self.ops(arrivals))
+        return st
+
+    # ---------------------------------------------------------------- plain
+    def run_plain(self, arrivals: list[Arrival]) -> RunStats:
+        """One frame per launch, in arrival order, each waited for before the next."""
+        lat = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a in arrivals:
+            while time.perf_counter() - t0 < a.t:
+                pass
+            s = self.specs[a.stream]
+            src = self._frame_view(a)
+            dst = self.ring.buf[:src.numel()]
+            with torch.cuda.stream(self.compute_stream):
+                dst.copy_(src.view(-1), non_blocking=True)
+            accumulate_batch([self.cors[a.stream]], [dst.view(a.T, s.F, s.N)], stream=self.compute_stream)
+            self._after_frame(a.stream)
+            self.compute_stream.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0 - a.t))
+        seconds = time.perf_counter() - t0 - arrivals[0].t
+        return RunStats("plain", len(arrivals), seconds, lat, self.ops(arrivals))
