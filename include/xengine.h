@@ -129,6 +129,22 @@ int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs
 int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
                              void* stream);
 
+/*
+ * corr_set_option -- per-handle launch knobs (the autotuner's controls; the
+ * results do not depend on them):
+ *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores for
+ *     half of each 64-sample chunk and dp4a for the other half, -1 = the
+ *     library default (1 unless the XE_PRODUCT=mma environment variable is set).
+ *   CORR_OPT_SPLIT: 0 = automatic time split, k >= 1 = cut the time axis into
+ *     k ranges (atomic adds when k > 1).
+ * A batched launch takes its product path from its first handle.
+ * Returns CORR_OK or CORR_EINVAL.
+ */
+#define CORR_OPT_PRODUCT 1
+#define CORR_OPT_SPLIT 2
+int corr_set_option(corr_handle_t* h, int option, int64_t value);
+int64_t corr_get_option(const corr_handle_t* h, int option);
+
 /* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit). */
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms);
 

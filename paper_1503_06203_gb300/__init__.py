@@ -11,10 +11,10 @@ import ctypes
 import numpy as np
 
 from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_MAX_SAMPLES, CORR_OK,
-                   XEngineError, check, last_error, lib)
+                   CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "plan_schedule", "correlate_noalloc", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "correlate_noalloc", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -151,6 +151,13 @@ class Correlator:
     @property
     def samples(self) -> int:
         return int(lib().corr_samples(self._h))
+
+    def set_option(self, option: int, value: int):
+        """Launch knobs (results never depend on them): CORR_OPT_PRODUCT, CORR_OPT_SPLIT."""
+        check(lib().corr_set_option(self._h, option, int(value)))
+
+    def get_option(self, option: int) -> int:
+        return int(lib().corr_get_option(self._h, option))
 
     @property
     def kernel_launches(self) -> int:

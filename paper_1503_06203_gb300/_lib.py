@@ -15,6 +15,8 @@ CORR_EOVERFLOW = -4
 CORR_ETIMEOUT = -5
 CORR_EBUSY = -6
 CORR_MAX_N = 16384
+CORR_OPT_PRODUCT = 1
+CORR_OPT_SPLIT = 2
 CORR_MAX_SAMPLES = 16777215
 
 # (name, restype, argtypes) for every symbol include/xengine.h declares
@@ -29,6 +31,8 @@ SIGNATURES = [
     ("corr_reset", _int, [_vp, _vp]),
     ("corr_accumulate_batch", _int, [_vp, _vp, _int, _vp]),
     ("corr_accumulate_batch_ex", _int, [_vp, _vp, _vp, _int, _vp]),
+    ("corr_set_option", _int, [_vp, _int, _i64]),
+    ("corr_get_option", _i64, [_vp, _int]),
     ("corr_synchronize", _int, [_vp, _i64]),
     ("corr_status", _int, [_vp]),
     ("corr_samples", _i64, [_vp]),

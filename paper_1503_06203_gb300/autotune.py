@@ -1,0 +1,110 @@
+"""Autotuner: the launch knobs that run a frame shape fastest on this GPU.
+
+Knobs (results never depend on them; see corr_set_option in include/xengine.h):
+the product path (tensor cores + dp4a, or tensor cores alone) and the time
+split (automatic, or a fixed number of ranges). For a frame shape (N, F, T)
+the tuner times every candidate with CUDA events on random frames and keeps
+the fastest in a JSON cache keyed by the GPU and the shape, so a shape is
+tuned once per GPU model.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import CORR_OPT_PRODUCT, CORR_OPT_SPLIT, Correlator
+
+CACHE_ENV = "XE_TUNE_CACHE"
+PRODUCTS = (1, 0)      # tensor cores + dp4a, tensor cores alone
+SPLITS = (0, 1, 2, 4)  # automatic, fixed
+
+
+def cache_path() -> str:
+    return os.environ.get(CACHE_ENV) or os.path.join(os.path.expanduser("~"), ".cache", "xengine_tune.json")
+
+
+def gpu_key() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|sm_{p.major}{p.minor}|{p.multi_processor_count}sm"
+
+
+def shape_key(N: int, F: int, T: int) -> str:
+    return f"N{N}_F{F}_T{T}"
+
+
+def candidates(T: int):
+    nch = -(-T // 64)
+    return [(p, s) for p in PRODUCTS for s in SPLITS if s <= nch]
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def save_cache(cache: dict, path: str | None = None):
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_config(c: Correlator, x, product: int, split: int, reps: int) -> float:
+    """Median ms of one frame accumulate under (product, split)."""
+    import torch
+    c.set_option(CORR_OPT_PRODUCT, product)
+    c.set_option(CORR_OPT_SPLIT, split)
+    for _ in range(2):
+        c.reset()
+        c.accumulate(x)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c.reset()
+        a.record()
+        c.accumulate(x)
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in ev)
+    return ms[len(ms) // 2]
+
+
+def tune(N: int, F: int, T: int, reps: int = 5, path: str | None = None, force: bool = False) -> dict:
+    """Time every candidate for (N, F, T) and cache the fastest; returns the cache entry."""
+    import torch
+    cache = load_cache(path)
+    g, k = gpu_key(), shape_key(N, F, T)
+    if not force and k in cache.get(g, {}):
+        return cache[g][k]
+    x = torch.randint(0, 256, (T, F, N), dtype=torch.uint8, device="cuda")
+    trials = []
+    with Correlator(N, F, T) as c:
+        for product, split in candidates(T):
+            trials.append({"product": product, "split": split, "ms": round(time_config(c, x, product, split, reps), 4)})
+    best = min(trials, key=lambda d: d["ms"])
+    entry = {"product": best["product"], "split": best["split"], "ms": best["ms"], "trials": trials}
+    cache = load_cache(path)  # re-read: another process may have written meanwhile
+    cache.setdefault(g, {})[k] = entry
+    save_cache(cache, path)
+    return entry
+
+
+def apply(c: Correlator, path: str | None = None, tune_if_missing: bool = True) -> dict | None:
+    """Set a correlator's knobs from the cache (tuning its shape first if it is missing)."""
+    cache = load_cache(path)
+    entry = cache.get(gpu_key(), {}).get(shape_key(c.N, c.F, c.T))
+    if entry is None and tune_if_missing:
+        entry = tune(c.N, c.F, c.T, path=path)
+    if entry is not None:
+        c.set_option(CORR_OPT_PRODUCT, entry["product"])
+        c.set_option(CORR_OPT_SPLIT, entry["split"])
+    return entry

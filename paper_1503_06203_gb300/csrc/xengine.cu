@@ -115,6 +115,8 @@ struct corr_handle {
   bool fresh = true;       // accumulators logically zero (memory may hold anything)
   int64_t samples = 0;
   int64_t launches = 0;    // kernels launched by this handle
+  int product = -1;        // CORR_OPT_PRODUCT (-1: library default)
+  int split_opt = 0;       // CORR_OPT_SPLIT (0: automatic)
   int sticky = CORR_OK;
   int32_t* d_err = nullptr;
   cudaEvent_t last = nullptr;
@@ -195,7 +197,7 @@ double imbalance(const std::vector<int4>& items, const std::vector<double>& cost
 // Pick the time split: the smallest that keeps the busiest CTA within 3% of
 // the mean (whole tiles need no atomics), else the best of the candidates.
 void plan_items(int32_t N, int32_t F, int32_t T, int64_t slots, std::vector<int4>& items, int64_t* split_out,
-                int64_t* grid_out) {
+                int64_t* grid_out, int64_t forced_split = 0) {
   std::vector<int2> tiles;
   std::vector<double> cost;
   frame_tiles(N, F, tiles, cost);
@@ -203,7 +205,9 @@ void plan_items(int32_t N, int32_t F, int32_t T, int64_t slots, std::vector<int4
   const int64_t nch = ceil_div(T, xe::kTC);
   int64_t best_split = 1;
   double best = 1e30;
+  if (forced_split > 0) best_split = std::min<int64_t>(forced_split, nch);
   for (int64_t split : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+    if (forced_split > 0) break;
     if (split > nch) break;
     std::vector<int4> cand;
     make_items(tiles, nch, split, cand);
@@ -226,7 +230,7 @@ int build_plan(corr_handle* h, int32_t T, Plan* pl) {
   const int64_t slots = static_cast<int64_t>(g_sms[h->device]) * g_blocks_per_sm[h->device];
   std::vector<int4> items;
   int64_t split = 1, grid = 1;
-  plan_items(h->N, h->F, T, slots, items, &split, &grid);
+  plan_items(h->N, h->F, T, slots, items, &split, &grid, h->split_opt);
   if (items.size() > static_cast<size_t>(INT32_MAX)) return fail(CORR_EINVAL, "schedule too large");
   XE_CHECK(h, cudaMalloc(&pl->d_items, items.size() * sizeof(int4)));
   XE_CHECK(h, cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
@@ -292,7 +296,7 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.B = h->B;
   a.vis = h->acc;
   a.fresh = h->fresh ? 1 : 0;
-  a.hybrid = g_hybrid;
+  a.hybrid = h->product < 0 ? g_hybrid : h->product;
   a.err = h->d_err;
   xe::corr_tile_kernel<<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
@@ -471,7 +475,7 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
   return CORR_OK;
 }
 
-int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err) {
+int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid) {
   if (b.exec) {
     cudaGraphExecDestroy(b.exec);
     b.exec = nullptr;
@@ -497,7 +501,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   a.B = 0;
   a.vis = nullptr;
   a.fresh = 0;
-  a.hybrid = g_hybrid;
+  a.hybrid = hybrid;
   a.err = err;
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
@@ -517,7 +521,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   b.key_frames = nframes;
   b.key_items = nitems;
   b.key_grid = grid;
-  b.key_hybrid = g_hybrid;
+  b.key_hybrid = hybrid;
   b.key_err = err;
   return CORR_OK;
 }
@@ -603,9 +607,10 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
     d.B = h->B;
     d.vis = h->acc;
   }
-  if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != g_hybrid ||
+  const int hybrid = hs[0]->product < 0 ? g_hybrid : hs[0]->product;
+  if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_err != hs[0]->d_err)
-    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err))) return rc;
+    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err, hybrid))) return rc;
   cudaError_t e = cudaGraphLaunch(b.exec, st);
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
   if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
@@ -754,6 +759,45 @@ int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs
 int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
                              void* stream) {
   return batch_impl(hs, inputs, Ts, n, stream);
+}
+
+int corr_set_option(corr_handle_t* h, int option, int64_t value) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (option == CORR_OPT_PRODUCT) {
+    if (value < -1 || value > 1) return fail(CORR_EINVAL, "CORR_OPT_PRODUCT must be -1, 0 or 1");
+    h->product = static_cast<int>(value);
+    return CORR_OK;
+  }
+  if (option == CORR_OPT_SPLIT) {
+    if (value < 0 || value > 4096) return fail(CORR_EINVAL, "CORR_OPT_SPLIT must be in [0, 4096]");
+    if (h->split_opt == value) return CORR_OK;
+    h->split_opt = static_cast<int>(value);
+    // rebuild the frame schedule (after the handle's queued work has read the old one)
+    if (h->has_last) {
+      cudaError_t e = cudaEventSynchronize(h->last);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    }
+    free_plan(&h->plan);
+    if ((rc = build_plan(h, h->T, &h->plan))) return rc;
+    if (h->plan_chunk.d_items) {
+      free_plan(&h->plan_chunk);
+      if ((rc = build_plan(h, h->hchunk_T, &h->plan_chunk))) return rc;
+    }
+    if (h->plan_tail.d_items) {
+      free_plan(&h->plan_tail);
+      if ((rc = build_plan(h, h->tail_T, &h->plan_tail))) return rc;
+    }
+    return CORR_OK;
+  }
+  return fail(CORR_EINVAL, "unknown option %d", option);
+}
+
+int64_t corr_get_option(const corr_handle_t* h, int option) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (option == CORR_OPT_PRODUCT) return h->product < 0 ? g_hybrid : h->product;
+  if (option == CORR_OPT_SPLIT) return h->split_opt;
+  return fail(CORR_EINVAL, "unknown option %d", option);
 }
 
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms) {

@@ -1,0 +1,44 @@
+"""Autotuner: cache keys and JSON round trip (CPU); tuning and every knob bit-exact (GPU)."""
+import numpy as np
+import pytest
+
+pytest.importorskip("torch")
+
+
+def test_cache_roundtrip_and_candidates(tmp_path):
+    from paper_1503_06203_gb300 import autotune
+    p = str(tmp_path / "tune.json")
+    assert autotune.load_cache(p) == {}
+    autotune.save_cache({"gpu": {autotune.shape_key(256, 4, 100): {"product": 0, "split": 2}}}, p)
+    assert autotune.load_cache(p)["gpu"]["N256_F4_T100"]["split"] == 2
+    assert (1, 4) in autotune.candidates(4096) and (0, 0) in autotune.candidates(4096)
+    assert all(s <= 1 for _, s in autotune.candidates(64))  # one chunk: no splits beyond 1
+
+
+@pytest.mark.gpu
+def test_every_knob_is_bit_exact_and_tuning_caches(tmp_path):
+    import torch
+
+    import oracle
+    import paper_1503_06203_gb300 as xe
+    import synth
+    from paper_1503_06203_gb300 import autotune
+    xe.build()
+    N, F, T = 192, 3, 1000
+    x = synth.gauss(N, F, T, 2.5, 31)
+    ref = oracle.visibilities(x)
+    xd = torch.from_numpy(x).cuda()
+    with xe.Correlator(N, F, T) as c:
+        for product, split in autotune.candidates(T):
+            c.set_option(xe.CORR_OPT_PRODUCT, product)
+            c.set_option(xe.CORR_OPT_SPLIT, split)
+            assert c.get_option(xe.CORR_OPT_PRODUCT) == product
+            c.reset()
+            c.accumulate(xd)
+            assert np.array_equal(c.readout().cpu().numpy().astype(np.int64), ref), (product, split)
+    p = str(tmp_path / "tune.json")
+    e = autotune.tune(N, F, T, reps=2, path=p)
+    assert (e["product"], e["split"]) in autotune.candidates(T) and len(e["trials"]) == len(autotune.candidates(T))
+    with xe.Correlator(N, F, T) as c:
+        assert autotune.apply(c, path=p, tune_if_missing=False)["ms"] == e["ms"]
+        assert c.get_option(xe.CORR_OPT_PRODUCT) == e["product"]
