@@ -133,7 +133,7 @@ int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inp
  * corr_set_option -- per-handle launch knobs (the autotuner's controls; the
  * results do not depend on them):
  *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores for
- *     half of each 64-sample chunk and dp4a for the other half, -1 = the
+ *     the first 96 of each 128-sample chunk and dp4a for the last 32, -1 = the
  *     library default (1 unless the XE_PRODUCT=mma environment variable is set).
  *   CORR_OPT_SPLIT: 0 = automatic time split, k >= 1 = cut the time axis into
  *     k ranges (atomic adds when k > 1).
@@ -180,7 +180,7 @@ int64_t corr_plan_tiles(int32_t N, int32_t tile, int32_t* bi_out, int32_t* bj_ou
  * corr_plan_schedule -- host-only scheduler query (no CUDA calls): the work
  * items the library launches for a frame of N, F, T on `ctas` resident CTAs.
  * Tiles are 64 x 64, band-major, row-major over each band's upper triangle
- * (Sec. II.C); time is cut into 64-sample chunks, and into `split` equal
+ * (Sec. II.C); time is cut into 128-sample chunks, and into `split` equal
  * ranges of chunks when whole tiles would leave the CTAs unbalanced. Item k
  * is {band f, bi | bj << 16, first chunk, end chunk} (4 int32 each in
  * items_out, at most items_cap items); CTA c runs items c, c + grid, ...

@@ -34,7 +34,7 @@ def shape_key(N: int, F: int, T: int) -> str:
 
 
 def candidates(T: int):
-    nch = -(-T // 64)
+    nch = -(-T // 128)
     return [(p, s) for p in PRODUCTS for s in SPLITS if s <= nch]
 
 

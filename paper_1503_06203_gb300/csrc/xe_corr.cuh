@@ -24,12 +24,12 @@
 namespace xe {
 
 constexpr int kTile = 64;                  // tile edge (elements)
-constexpr int kTC = 64;                    // time samples per chunk (pipeline stage)
+constexpr int kTC = 128;                   // time samples per chunk (pipeline stage)
 #ifndef XE_STAGES
-#define XE_STAGES 6
+#define XE_STAGES 4
 #endif
 #ifndef XE_PLANE_BUFS
-#define XE_PLANE_BUFS 4
+#define XE_PLANE_BUFS 3
 #endif
 constexpr int kStages = XE_STAGES;         // TMA ring depth
 constexpr int kPlaneBufs = XE_PLANE_BUFS;  // unpacked-plane buffers between the unpack and product warps
@@ -66,7 +66,7 @@ struct CorrArgs {
   int64_t B;            // N(N+1)/2
   int32_t* vis;         // [F][B][2] accumulators
   int32_t fresh;        // 1: accumulators hold no integration yet (whole tiles store)
-  int32_t hybrid;       // 1: samples 32..63 of each chunk run on dp4a (chunk_hybrid), 0: tensor cores only
+  int32_t hybrid;       // 0: tensor cores only; 1: the last 32 of each chunk's 128 samples on dp4a
   int32_t* err;         // device error word
 };
 
@@ -79,17 +79,19 @@ struct __align__(128) CorrSmem {
   uint64_t pempty[kPlaneBufs];  // plane buffer read (4 product warps)
 };
 
-// Swizzle of a plane: 16-byte chunk c of row e sits at chunk c ^ f(e). f
-// makes the ldmatrix reads (8 consecutive rows, one chunk) and the unpack
-// stores below (rows 4eg + slot across a half-warp) free of bank conflicts.
+// Swizzle of a plane (rows of kTC = 128 bytes, 8 chunks of 16): chunk c of
+// row e sits at chunk c ^ f(e), f(e) = (e ^ (e >> 3)) & 7. Eight consecutive
+// rows then hit eight different 16-byte bank groups (ldmatrix, the dp4a
+// operand loads), and so do the unpack stores below (rows 4eg + slot across a
+// quarter-warp).
 __device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
-  const int f = ((e >> 1) ^ (e >> 3)) & 3;
+  const int f = (e ^ (e >> 3)) & 7;
   return static_cast<uint32_t>(e * kTC + ((chunk ^ f) << 4));
 }
 
 // ---- unpack: packed box [time][element] -> planes [element][time] --------------
 //
-// A thread owns 4 elements (4eg..4eg+3) x 16 samples (16tg..16tg+15) of one
+// A call handles 4 elements (4eg..4eg+3) x 16 samples (16tg..16tg+15) of one
 // block. It loads 16 row words, transposes 4x4 byte blocks with prmt, then
 // turns each 4-sample word into the plane bytes with carry-free byte
 // arithmetic (v = nibble in [0, 15]):
@@ -146,7 +148,7 @@ __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, ui
   }
 }
 
-// ---- product: one 64-sample chunk of a warp's 16 x 16 piece of the tile --------
+// ---- product: one 128-sample chunk of a warp's 16 x 16 piece of the tile --------
 // acc[0] = P1, acc[1] = P2, acc[2] = Q, each over the piece's two 16 x 8
 // sub-tiles (ni = 0, 1). Planes are addressed as shared-memory offsets: A side
 // slot p at a_base + p*kPlaneBytes; B side slots 0-1 at b01_base +
@@ -193,38 +195,42 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // ---- product, hybrid: tensor cores and the integer ALU side by side -----------
 // The tensor pipe and the dp4a pipe of an SM sub-partition run concurrently
 // and at about the same rate on this GPU. A warp runs the three products for
-// samples 0..31 of the chunk on the tensor cores (one k-step) and for samples
-// 32..63 with dp4a (4 samples per instruction), accumulating both into the
-// same registers: thread (g, q) owns, per sub-tile ni, the entries (row
-// g + 8h, column ni*8 + 2q + c) of the MMA accumulator layout, so its dp4a
-// work is those entries' dot products. Each of the 6 blocks below issues one
-// MMA (plane k/2, sub-tile k%2) and 32 dp4a (8 samples of one plane).
-template <int sel>
+// the chunk's first kMmaK k-steps (32 samples each) on the tensor cores and
+// for the remaining samples with dp4a (4 samples per instruction),
+// accumulating both into the same registers: thread (g, q) owns, per
+// sub-tile ni, the entries (row g + 8h, column ni*8 + 2q + c) of the MMA
+// accumulator layout, so its dp4a work is those entries' dot products. The
+// dp4a work comes in blocks of 8 samples of one plane; the MMAs are spread
+// evenly over the blocks.
+template <int sel, int kMmaK>
 __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
                                              int lane, int32_t (&acc)[3][2][4]) {
   constexpr int kNi0 = sel == kSelN1 ? 1 : 0;  // first column sub-tile
   constexpr int kNi = sel == kSelAll ? 2 : 1;   // column sub-tiles
+  constexpr int kMmas = kMmaK * 6;              // (k-step, plane, sub-tile)
+  constexpr int kBlocks = (kTC - 32 * kMmaK) / 8 * 3;  // (8 samples, plane)
   const int g = lane >> 2, q = lane & 3;
   const int arow = pr * 16 + (lane & 15);
   const int brow = pc * 16 + (lane & 7) + ((lane >> 4) << 3);
   const int ahalf = lane >> 4, bhalf = (lane >> 3) & 1;
   uint32_t fa[4], fb[2][2];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    // ---- tensor cores: k-step 0 (samples 0..31), one MMA every other block ----
-    if ((k & 1) == 0) {
-      const int mk = k >> 1, mpl = mk >> 1, mni = mk & 1;
+  for (int k = 0; k < kBlocks; ++k) {
+    // ---- tensor cores: this block's share of the MMAs ----
+#pragma unroll
+    for (int m = k * kMmas / kBlocks; m < (k + 1) * kMmas / kBlocks; ++m) {
+      const int mks = m / 6, mpl = (m / 2) % 3, mni = m & 1;
       if (mni == 0) {
         const uint32_t pa = a_base + mpl * kPlaneBytes;
         const uint32_t pb = mpl < 2 ? b01_base + mpl * kPlaneBytes : b2_base;
-        ldsm_x4(pa + plane_off(arow, ahalf), fa[0], fa[1], fa[2], fa[3]);
-        ldsm_x4(pb + plane_off(brow, bhalf), fb[0][0], fb[0][1], fb[1][0], fb[1][1]);
+        ldsm_x4(pa + plane_off(arow, 2 * mks + ahalf), fa[0], fa[1], fa[2], fa[3]);
+        ldsm_x4(pb + plane_off(brow, 2 * mks + bhalf), fb[0][0], fb[0][1], fb[1][0], fb[1][1]);
       }
       if (sub_on(sel, mni)) mma_s8_16832(acc[mpl][mni], fa[0], fa[1], fa[2], fa[3], fb[mni][0], fb[mni][1]);
     }
-    // ---- integer ALU: samples 32 + 8*grp .. +7 of plane dpl ----
+    // ---- integer ALU: samples 32*kMmaK + 8*grp .. +7 of plane dpl ----
     const int grp = k / 3, dpl = k % 3;
-    const int s0 = 32 + 8 * grp, chunk = s0 >> 4, inner = s0 & 15;
+    const int s0 = 32 * kMmaK + 8 * grp, chunk = s0 >> 4, inner = s0 & 15;
     const uint32_t pa = a_base + dpl * kPlaneBytes;
     const uint32_t pb = dpl < 2 ? b01_base + dpl * kPlaneBytes : b2_base;
     uint32_t av[2][2], bv[2][2][2];  // [h][word], [n][c][word]
@@ -381,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     // ================= unpack warps (+ TMA issue) =================
     const int uw = warp - kMmaWarps;  // 0..3
     const bool producer = uw == 0 && lane == 0;
-    const int eg = lane & 15, p = lane >> 4, tg = 2 * (uw & 1) + p;
+    const int eg = lane & 15, p = lane >> 4, tg = 2 * uw + p;  // samples 16tg..16tg+15 of each chunk
     Walk ld;  // the TMA issuer walks the same units, kStages ahead
     ld.start(args, blockIdx.x, gridDim.x);
     uint32_t issued = 0;
@@ -418,21 +424,20 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         break;
       }
       const int nvalid = x.T - x.c * kTC;
-      const int blk = diag ? 0 : (uw >> 1);
-      const uint8_t* box = sm.box[s][blk];
-      uint32_t pl0 = smem_u32(sm.plane[buf][blk][kPxr]);
-      uint32_t pl1 = smem_u32(sm.plane[buf][blk][kPxi]);
-      uint32_t pl2 = smem_u32(sm.plane[buf][blk][kPsd]);
-      bool side_b = blk == 1;
-      if (diag && uw >= 2) {  // diagonal tile: the last two unpack warps make the B side's xr - xi plane
-        pl0 = pl1 = 0;
-        pl2 = smem_u32(sm.plane[buf][1][kPsd]);
-        side_b = true;
+      // two units per thread: the row side (j = 0) and the column side (j = 1); a
+      // diagonal tile's column side is only its xr - xi plane, from the same box
+#pragma unroll 1
+      for (int j = 0; j < 2; ++j) {
+        const uint8_t* box = sm.box[s][diag ? 0 : j];
+        uint32_t pl0 = smem_u32(sm.plane[buf][j][kPxr]);
+        uint32_t pl1 = smem_u32(sm.plane[buf][j][kPxi]);
+        const uint32_t pl2 = smem_u32(sm.plane[buf][j][kPsd]);
+        if (diag && j == 1) pl0 = pl1 = 0;
+        if (nvalid >= kTC)
+          unpack_unit<false>(box, pl0, pl1, pl2, j == 1, eg, tg, p, kTC);
+        else
+          unpack_unit<true>(box, pl0, pl1, pl2, j == 1, eg, tg, p, nvalid);
       }
-      if (nvalid >= kTC)
-        unpack_unit<false>(box, pl0, pl1, pl2, side_b, eg, tg, p, kTC);
-      else
-        unpack_unit<true>(box, pl0, pl1, pl2, side_b, eg, tg, p, nvalid);
       mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
       mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
       if (producer && ld.valid()) {  // refill slot s once every unpack thread is done with it
@@ -481,13 +486,13 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
       const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
       const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
-      if (args.hybrid && ksteps == kTC / 32) {  // (a ragged last chunk's zero samples take either path)
+      if (args.hybrid == 1 && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
         if (sel == kSelAll)
-          chunk_hybrid<kSelAll>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelAll, 3>(a_base, b01, b2, pr, pc, lane, acc);
         else if (sel == kSelN0)
-          chunk_hybrid<kSelN0>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelN0, 3>(a_base, b01, b2, pr, pc, lane, acc);
         else
-          chunk_hybrid<kSelN1>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelN1, 3>(a_base, b01, b2, pr, pc, lane, acc);
       } else if (sel == kSelAll) {
         chunk_mma<kSelAll>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
       } else if (sel == kSelN0) {

@@ -103,7 +103,7 @@ def test_schedule_covers_every_unit_once(xe, N, F, T, ctas):
     items, grid = xe.plan_schedule(N, F, T, ctas)
     nb = -(-N // 64)
     per_band = nb * (nb + 1) // 2
-    nch = -(-T // 64)
+    nch = -(-T // 128)
     assert 1 <= grid <= ctas
     f, bi, bj, c0, c1 = items[:, 0], items[:, 1] & 0xFFFF, items[:, 1] >> 16, items[:, 2], items[:, 3]
     assert (bi <= bj).all() and (bj < nb).all() and (f < F).all() and (0 <= c0).all() and (c0 < c1).all()

@@ -12,7 +12,7 @@ def test_cache_roundtrip_and_candidates(tmp_path):
     autotune.save_cache({"gpu": {autotune.shape_key(256, 4, 100): {"product": 0, "split": 2}}}, p)
     assert autotune.load_cache(p)["gpu"]["N256_F4_T100"]["split"] == 2
     assert (1, 4) in autotune.candidates(4096) and (0, 0) in autotune.candidates(4096)
-    assert all(s <= 1 for _, s in autotune.candidates(64))  # one chunk: no splits beyond 1
+    assert all(s <= 1 for _, s in autotune.candidates(128))  # one chunk: no splits beyond 1
 
 
 @pytest.mark.gpu

@@ -48,7 +48,7 @@ def assert_exact(V_gpu, V_ref):
 
 
 SHAPES = [
-    # (N, F, T): tiny config, ragged N around the 64-element tile, ragged T around the 64-sample stage
+    # (N, F, T): tiny config, ragged N around the 64-element tile, ragged T around the 128-sample stage
     (16, 4, 256), (1, 1, 16), (2, 3, 17), (15, 2, 100), (17, 3, 33), (32, 1, 1), (63, 2, 64), (64, 2, 64),
     (65, 1, 130), (100, 3, 300), (127, 1, 129), (128, 2, 63), (129, 2, 257), (200, 2, 1000), (256, 4, 1000),
     (300, 2, 640), (512, 1, 128), (48, 5, 4096),
