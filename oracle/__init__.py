@@ -9,8 +9,8 @@ upper triangle of Sec. II.A, the excess-8 decoding of Sec. III), in C with
 int64 accumulators: see ``xcorr_oracle.c``. Parity status: pinned (the
 ``tests/test_oracle_*.py`` pins: hand-worked cases, brute force with Python
 complex numbers, a numpy matmul special case, Hermitian symmetry, autos,
-the identical-sequence closed form, the Freivalds identity and the Eq. 3
-identity).
+the identical-sequence closed form, the Freivalds identity, the Eq. 3
+identity, and the lag-shift pins).
 """
 from __future__ import annotations
 
@@ -52,6 +52,8 @@ def _load():
         lib.oracle_freivalds_rhs.restype = ci
         lib.oracle_offset_terms.argtypes = [vp, i64, i64, i64, vp]
         lib.oracle_offset_terms.restype = ci
+        lib.oracle_shift_lags.argtypes = [vp, i64, i64, i64, vp, vp]
+        lib.oracle_shift_lags.restype = ci
         _lib = lib
     return _lib
 
@@ -131,6 +133,18 @@ def offset_terms(x: np.ndarray) -> np.ndarray:
     rc = _load().oracle_offset_terms(x.ctypes.data, N, F, T, out.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_offset_terms failed ({rc})")
+    return out
+
+
+def shift_lags(x: np.ndarray, lags) -> np.ndarray:
+    """Per-element time shift (Sec. IV): out[t,f,i] = x[t - lag_i, f, i], zero (0x88) outside the frame."""
+    N, F, T = _check_x(x)
+    lags = np.ascontiguousarray(lags, dtype=np.int32)
+    assert lags.shape == (N,)
+    out = np.empty_like(x)
+    rc = _load().oracle_shift_lags(x.ctypes.data, N, F, T, lags.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_shift_lags failed ({rc})")
     return out
 
 

@@ -274,3 +274,21 @@ int oracle_offset_terms(const uint8_t* x, int64_t N, int64_t F, int64_t T, int64
   free(sm);
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Per-element integer time shift before correlation (Sec. IV: a kernel that
+ * shifts individual elements by integer time steps, to create or compensate
+ * lags). out[t,f,i] = in[t - lag_i, f, i] when 0 <= t - lag_i < T, else the
+ * code of 0 + 0i (0x88): samples shifted in from outside the frame are zero.
+ */
+int oracle_shift_lags(const uint8_t* in, int64_t N, int64_t F, int64_t T, const int32_t* lags, uint8_t* out) {
+  if (!in || !out || !lags || N < 1 || F < 1 || T < 0) return -1;
+  for (int64_t t = 0; t < T; ++t)
+    for (int64_t f = 0; f < F; ++f)
+      for (int64_t i = 0; i < N; ++i) {
+        const int64_t src = t - (int64_t)lags[i];
+        out[(t * F + f) * N + i] = (src >= 0 && src < T) ? in[(src * F + f) * N + i] : (uint8_t)0x88;
+      }
+  return 0;
+}

@@ -1,0 +1,53 @@
+"""Failure handling on the GPU without faulting it: host deadlines, failed allocations, bad calls."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xe():
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    return xe
+
+
+def test_synchronize_deadline_runs_out_while_busy(xe):
+    """A short host deadline on a long frame returns CORR_ETIMEOUT; waiting longer then succeeds."""
+    import torch
+    N, F, T = 2048, 16, 16384  # about 0.3 s of work
+    x = torch.randint(0, 256, (T, F, N), dtype=torch.uint8, device="cuda")
+    with xe.Correlator(N, F, T) as c:
+        torch.cuda.synchronize()
+        c.accumulate(x)
+        with pytest.raises(xe.XEngineError) as ei:
+            c.synchronize(timeout_ms=0)
+        assert ei.value.code == xe.CORR_ETIMEOUT
+        c.synchronize(timeout_ms=60000)
+        assert c.status() == 0  # a host deadline is not a device fault: nothing sticky
+
+
+def test_allocation_failure_is_reported(xe):
+    """Accumulators larger than the device's memory: CORR_ENOMEM from corr_create, nothing leaked."""
+    import torch
+    from paper_1503_06203_gb300._lib import CORR_ENOMEM, lib
+    free0, total = torch.cuda.mem_get_info()
+    N = 16384
+    F = int(total // (N * (N + 1) // 2 * 8)) + 2  # accumulators larger than the whole device
+    assert not lib().corr_create(N, F, 1024)
+    assert "cudaMalloc" in xe.last_error() or "accumulators" in xe.last_error()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20)
+    with xe.Correlator(64, 1, 128) as c:  # the device still works
+        c.accumulate(torch.zeros((128, 1, 64), dtype=torch.uint8, device="cuda"))
+        assert int(c.readout()[0, 0, 0]) == 128 * 128
+
+
+def test_bad_frames_rejected_before_launch(xe):
+    import torch
+    with xe.Correlator(64, 2, 256) as c:
+        n0 = c.kernel_launches
+        with pytest.raises(ValueError):
+            c.accumulate(torch.zeros((256, 2, 63), dtype=torch.uint8, device="cuda"))
+        from paper_1503_06203_gb300._lib import CORR_EINVAL, lib
+        assert lib().corr_accumulate(c.handle, None, None) == CORR_EINVAL
+        assert c.kernel_launches == n0 and c.status() == 0

@@ -208,3 +208,37 @@ def test_extreme_magnitudes():
 def test_thread_count_invariance():
     x = synth.gauss(45, 5, 100, 2.5, 16)
     assert np.array_equal(oracle.visibilities(x, 1), oracle.visibilities(x, 7))
+
+
+def test_shift_lags_pins():
+    """Sec. IV lag shift: zero lag is the identity; a lag moves samples in time, zero-filled."""
+    N, F, T = 6, 2, 40
+    x = synth.uniform(N, F, T, 21)
+    assert np.array_equal(oracle.shift_lags(x, np.zeros(N)), x)
+    lags = np.array([0, 3, -2, T + 5, -T, 1], dtype=np.int32)
+    y = oracle.shift_lags(x, lags)
+    for i, L in enumerate(lags):
+        for t in range(T):
+            src = t - L
+            want = x[src, :, i] if 0 <= src < T else np.full(F, 0x88, np.uint8)
+            assert np.array_equal(y[t, :, i], want), (i, t)
+    # shifting by L then by -L restores the samples that stayed inside the frame
+    z = oracle.shift_lags(oracle.shift_lags(x, lags), -lags)
+    for i, L in enumerate(lags):
+        keep = [t for t in range(T) if 0 <= t + L < T]
+        assert np.array_equal(z[keep, :, i], x[keep, :, i])
+
+
+def test_shift_lags_compensates_a_delay():
+    """Element 1 is element 0 delayed by d samples; shifting element 1 by -d aligns them, so
+    V01 becomes element 0's autocorrelation over the samples both still hold."""
+    N, F, T, d = 2, 1, 200, 17
+    base = synth.gauss(1, F, T, 2.5, 22)[:, :, 0]
+    x = np.full((T, F, N), 0x88, dtype=np.uint8)
+    x[:, :, 0] = base
+    x[d:, :, 1] = base[:T - d]          # delayed copy
+    y = oracle.shift_lags(x, np.array([0, -d], dtype=np.int32))
+    V = oracle.visibilities(y)
+    part = np.ascontiguousarray(x[:T - d, :, :1])  # samples 0 .. T-d-1 of element 0
+    auto = oracle.visibilities(part)[0, 0]
+    assert tuple(V[0, 1]) == (auto[0], 0)
