@@ -54,6 +54,8 @@ def _load():
         lib.oracle_offset_terms.restype = ci
         lib.oracle_shift_lags.argtypes = [vp, i64, i64, i64, vp, vp]
         lib.oracle_shift_lags.restype = ci
+        lib.oracle_gated.argtypes = [vp, i64, i64, i64, i64, i64, i64, vp]
+        lib.oracle_gated.restype = ci
         _lib = lib
     return _lib
 
@@ -146,6 +148,16 @@ def shift_lags(x: np.ndarray, lags) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"oracle_shift_lags failed ({rc})")
     return out
+
+
+def gated(x: np.ndarray, G: int, period: int, phase: int = 0) -> np.ndarray:
+    """Gated visibilities (Sec. IV), int64 [G][F][B][2]; gate(t) = ((t + phase) % period) * G // period."""
+    N, F, T = _check_x(x)
+    V = np.empty((G, F, baselines(N), 2), dtype=np.int64)
+    rc = _load().oracle_gated(x.ctypes.data, N, F, T, G, period, phase, V.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"oracle_gated failed ({rc})")
+    return V
 
 
 def timed_visibilities(x: np.ndarray, nthreads: int | None = None):

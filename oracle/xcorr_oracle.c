@@ -292,3 +292,35 @@ int oracle_shift_lags(const uint8_t* in, int64_t N, int64_t F, int64_t T, const 
       }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Gated correlation (Sec. IV: the products are binned by time into several
+ * gates, for periodic signals such as pulsars or calibration sources).
+ * Reading: gate(t) = floor(((t + phase) mod period) * G / period), i.e. G
+ * equal phase bins of a repeating period. V[g][f][p][2] accumulates Eq. 1's
+ * products of the samples with gate(t) = g; packed like oracle_visibilities.
+ */
+int oracle_gated(const uint8_t* x, int64_t N, int64_t F, int64_t T, int64_t G, int64_t period, int64_t phase,
+                 int64_t* V) {
+  if (!x || !V || N < 1 || F < 1 || T < 0 || G < 1 || period < 1 || phase < 0) return -1;
+  const int64_t B = N * (N + 1) / 2;
+  int64_t* gate = (int64_t*)malloc(sizeof(int64_t) * (size_t)(T ? T : 1));
+  if (!gate) return -2;
+  for (int64_t t = 0; t < T; ++t) gate[t] = ((t + phase) % period) * G / period;
+  memset(V, 0, sizeof(int64_t) * 2 * (size_t)(G * F * B));
+  for (int64_t t = 0; t < T; ++t)
+    for (int64_t f = 0; f < F; ++f) {
+      const uint8_t* row = x + (t * F + f) * N;
+      int64_t* Vg = V + 2 * (gate[t] * F + f) * B;
+      for (int64_t i = 0; i < N; ++i)
+        for (int64_t j = i; j < N; ++j) {
+          const int64_t xr = re_of(row[i]), xi = im_of(row[i]), yr = re_of(row[j]), yi = im_of(row[j]);
+          int64_t* o = Vg + 2 * (i * N - i * (i - 1) / 2 + (j - i));
+          o[0] += xr * yr + xi * yi;
+          o[1] += xi * yr - xr * yi;
+        }
+    }
+  free(gate);
+  return 0;
+}

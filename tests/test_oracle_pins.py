@@ -242,3 +242,36 @@ def test_shift_lags_compensates_a_delay():
     part = np.ascontiguousarray(x[:T - d, :, :1])  # samples 0 .. T-d-1 of element 0
     auto = oracle.visibilities(part)[0, 0]
     assert tuple(V[0, 1]) == (auto[0], 0)
+
+
+def test_gated_pins():
+    """Sec. IV gating: one gate is the plain correlation; gates partition the samples."""
+    x = synth.gauss(12, 2, 300, 2.5, 23)
+    plain = oracle.visibilities(x)
+    assert np.array_equal(oracle.gated(x, 1, 37, 5)[0], plain)
+    for G, period, phase in [(4, 64, 0), (3, 50, 17), (8, 300, 299)]:
+        V = oracle.gated(x, G, period, phase)
+        assert np.array_equal(V.sum(axis=0), plain)
+    # hand-derived gates for period 4, G 2, phase 1: t = 0..7 -> 0,1,1,0,0,1,1,0
+    T = 8
+    xs = np.full((T, 1, 2), 0x88, dtype=np.uint8)
+    for t in range(T):
+        xs[t, 0, 0] = 0x98 + t  # element 0 = 1 + (t)i... distinct samples
+    V = oracle.gated(xs, 2, 4, 1)
+    gates = [0, 1, 1, 0, 0, 1, 1, 0]
+    for g in range(2):
+        want = sum(int((xs[t, 0, 0] >> 4) - 8) ** 2 + int((xs[t, 0, 0] & 15) - 8) ** 2 for t in range(T) if gates[t] == g)
+        assert V[g, 0, 0, 0] == want
+
+
+def test_gated_pulse_closed_form():
+    """A common pulse in gate 0's window only: gate 0 holds (sum |q|^2, 0) on every baseline, others zero."""
+    N, F, T, G, period = 16, 2, 512, 4, 64
+    q = synth.gauss(1, 1, T, 3.0, 24)[:, 0, 0]
+    x = np.full((T, F, N), 0x88, dtype=np.uint8)
+    on = np.array([((t % period) * G // period) == 0 for t in range(T)])
+    x[on] = q[on, None, None]
+    V = oracle.gated(x, G, period, 0)
+    qr, qi = (q[on] >> 4).astype(np.int64) - 8, (q[on] & 15).astype(np.int64) - 8
+    assert (V[0, :, :, 0] == int((qr * qr + qi * qi).sum())).all() and not V[0, :, :, 1].any()
+    assert not V[1:].any()
