@@ -130,6 +130,21 @@ int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inp
                              void* stream);
 
 /*
+ * corr_shift_lags -- shift every element of a frame by its own integer
+ * number of samples before correlation (Sec. IV: lags between elements, e.g.
+ * unequal cable lengths, are created or compensated in software):
+ *   out[t][f][i] = in[t - lags[i]][f][i]  when 0 <= t - lags[i] < T,
+ *   out[t][f][i] = 0x88 (the code of 0 + 0i) otherwise.
+ * in_dev, out_dev: distinct device frames uint8 [T][F][N]; out_dev 4-byte
+ * aligned when N % 4 == 0. lags_dev: device int32 [N], any sign (a lag of T
+ * or more in magnitude empties the element). Asynchronous on `stream`; the
+ * caller keeps the buffers alive. Samples shifted past the frame's ends are
+ * dropped (each frame is shifted on its own).
+ */
+int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t F, int32_t T, const int32_t* lags_dev,
+                    void* stream);
+
+/*
  * corr_set_option -- per-handle launch knobs (the autotuner's controls; the
  * results do not depend on them):
  *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores for
@@ -144,6 +159,20 @@ int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inp
 #define CORR_OPT_SPLIT 2
 int corr_set_option(corr_handle_t* h, int option, int64_t value);
 int64_t corr_get_option(const corr_handle_t* h, int option);
+
+/*
+ * corr_accumulate_gated -- gated correlation of one frame (Sec. IV: the
+ * products are binned by time into gates, for periodic signals such as
+ * pulsars or calibration sources). Sample t of the frame belongs to gate
+ *   g(t) = floor(((t + phase) mod period) * G / period)
+ * and its products are added to gates[g]'s accumulators. gates: G distinct
+ * handles with the same N and F (their T is not used); packed_dev: device
+ * frame uint8 [T][F][N]; 1 <= period, 0 <= phase < period. Each maximal run
+ * of samples in one gate is a segment; at most 2047 segments per call
+ * (CORR_EINVAL beyond). Asynchronous on `stream`, one launch for all gates.
+ */
+int corr_accumulate_gated(corr_handle_t* const* gates, int G, const uint8_t* packed_dev, int32_t T, int32_t period,
+                          int32_t phase, void* stream);
 
 /* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit). */
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms);

@@ -14,7 +14,7 @@ from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_
                    CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "plan_schedule", "correlate_noalloc", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "correlate_noalloc", "shift_lags", "accumulate_gated", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -166,6 +166,32 @@ class Correlator:
     @property
     def handle(self):
         return self._h
+
+
+def shift_lags(x, lags, out=None, stream=None):
+    """Per-element time shift before correlation (Sec. IV): out[t,f,i] = x[t - lags[i], f, i], zero outside.
+
+    x: CUDA uint8 [T][F][N]; lags: CUDA int32 [N]; returns `out` (allocated if None).
+    """
+    import torch
+    T, F, N = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    assert lags.is_cuda and lags.dtype == torch.int32 and lags.numel() == N and lags.is_contiguous()
+    check(lib().corr_shift_lags(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), N, F, T,
+                                ctypes.c_void_p(lags.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def accumulate_gated(gates, x, period: int, phase: int = 0, stream=None):
+    """Gated correlation (Sec. IV): sample t of frame x goes to gates[((t + phase) % period) * G // period]."""
+    G = len(gates)
+    T, F, N = x.shape
+    for c in gates:
+        if (c.N, c.F) != (N, F):
+            raise ValueError("gate correlators must match the frame's N and F")
+    hs = (ctypes.c_void_p * G)(*[c._h.value for c in gates])
+    check(lib().corr_accumulate_gated(hs, G, ctypes.c_void_p(x.data_ptr()), T, period, phase, _stream_ptr(stream)))
 
 
 def correlate_noalloc(x, out, status=None, stream=None):

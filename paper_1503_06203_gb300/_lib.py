@@ -31,6 +31,8 @@ SIGNATURES = [
     ("corr_reset", _int, [_vp, _vp]),
     ("corr_accumulate_batch", _int, [_vp, _vp, _int, _vp]),
     ("corr_accumulate_batch_ex", _int, [_vp, _vp, _vp, _int, _vp]),
+    ("corr_accumulate_gated", _int, [_vp, _int, _vp, _i32, _i32, _i32, _vp]),
+    ("corr_shift_lags", _int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     ("corr_set_option", _int, [_vp, _int, _i64]),
     ("corr_get_option", _i64, [_vp, _int]),
     ("corr_synchronize", _int, [_vp, _i64]),

@@ -52,6 +52,8 @@ struct __align__(64) FrameDesc {
   int32_t N, T, nch, fresh;
   int64_t B;         // N(N+1)/2
   int32_t* vis;      // [F][B][2] accumulators of the frame's handle
+  int32_t t0;        // samples before t0 count as zero (gated segments); 0 for whole frames
+  int32_t atomic;    // 1: add atomically (several segments feed the same accumulators)
 };
 
 struct CorrArgs {
@@ -103,14 +105,14 @@ __device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
 // free of bank conflicts; runtime prmt selectors undo both reorderings.
 template <bool kMasked>
 __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, uint32_t pl1, uint32_t pl2,
-                                            bool side_b, int eg, int tg, int p, int nvalid) {
+                                            bool side_b, int eg, int tg, int p, int lo, int hi) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(box);
   uint32_t r[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     const int t = 16 * tg + (k ^ p);
     r[k] = w[t * (kTile / 4) + eg];
-    if (kMasked) r[k] = t < nvalid ? r[k] : 0x88888888u;  // 0x88 decodes to 0 + 0i
+    if (kMasked) r[k] = (t >= lo && t < hi) ? r[k] : 0x88888888u;  // rows outside [lo, hi) read as 0 + 0i
   }
   const int s = eg & 1;
   const uint32_t selA = p ? 0x1504u : 0x5140u;  // interleave two rows, bytes 0-1
@@ -316,7 +318,7 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // item's frame's (from its descriptor in a batch, else from args); the writer
 // reads the rest when it needs it.
 struct Walk {
-  int item, c, f, bi, bj, c1, frame, T, nch;
+  int item, c, f, bi, bj, c1, frame, T, nch, T0;
   const int4* items;
   const FrameDesc* frames;
   int nitems, stride;
@@ -334,6 +336,7 @@ struct Walk {
           frame = fr;
           T = frames[fr].T;
           nch = frames[fr].nch;
+          T0 = frames[fr].t0;
         }
       } else {
         f = w.x;
@@ -349,6 +352,7 @@ struct Walk {
     frame = -1;
     T = a.T;
     nch = a.nch;
+    T0 = 0;
     load();
   }
   __device__ __forceinline__ bool valid() const { return item < nitems; }
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         ok = false;
         break;
       }
-      const int nvalid = x.T - x.c * kTC;
+      const int lo = x.T0 - x.c * kTC, hi = x.T - x.c * kTC;  // valid rows of this chunk
       // two units per thread: the row side (j = 0) and the column side (j = 1); a
       // diagonal tile's column side is only its xr - xi plane, from the same box
 #pragma unroll 1
@@ -433,10 +437,10 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         uint32_t pl1 = smem_u32(sm.plane[buf][j][kPxi]);
         const uint32_t pl2 = smem_u32(sm.plane[buf][j][kPsd]);
         if (diag && j == 1) pl0 = pl1 = 0;
-        if (nvalid >= kTC)
-          unpack_unit<false>(box, pl0, pl1, pl2, j == 1, eg, tg, p, kTC);
+        if (lo <= 0 && hi >= kTC)
+          unpack_unit<false>(box, pl0, pl1, pl2, j == 1, eg, tg, p, 0, kTC);
         else
-          unpack_unit<true>(box, pl0, pl1, pl2, j == 1, eg, tg, p, nvalid);
+          unpack_unit<true>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi);
       }
       mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
       mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       const bool whole = w.z == 0 && w.w == x.nch;
       const FrameDesc* d = args.frames ? &args.frames[x.frame] : nullptr;
       const int fresh = d ? d->fresh : args.fresh;
-      const int mode = whole ? (fresh ? 0 : 1) : 2;
+      const int mode = (d && d->atomic) ? 2 : (whole ? (fresh ? 0 : 1) : 2);
       if (sel != kSelIdle)
         write_piece(d ? d->N : args.N, d ? d->B : args.B, d ? d->vis : args.vis, x.f, x.bi * kTile, x.bj * kTile, pr,
                     pc, lane, mode, sel, acc);

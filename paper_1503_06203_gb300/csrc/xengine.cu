@@ -13,6 +13,7 @@
 
 #include "xengine.h"
 #include "xe_corr.cuh"
+#include "xe_lags.cuh"
 
 namespace {
 
@@ -75,6 +76,13 @@ int device_setup(int dev) {
 }
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A failed allocation leaves the runtime's last-error slot set; clear it so a
+// later launch check does not report it as the launch's own error.
+int alloc_failed(const char* what, size_t bytes, cudaError_t e) {
+  cudaGetLastError();
+  return fail(CORR_ENOMEM, "%s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+}
 
 // Product path: 1 = tensor cores + dp4a (chunk_hybrid), 0 = tensor cores only.
 // XE_PRODUCT=mma in the environment selects the tensor-core-only path.
@@ -232,7 +240,11 @@ int build_plan(corr_handle* h, int32_t T, Plan* pl) {
   int64_t split = 1, grid = 1;
   plan_items(h->N, h->F, T, slots, items, &split, &grid, h->split_opt);
   if (items.size() > static_cast<size_t>(INT32_MAX)) return fail(CORR_EINVAL, "schedule too large");
-  XE_CHECK(h, cudaMalloc(&pl->d_items, items.size() * sizeof(int4)));
+  cudaError_t ae = cudaMalloc(&pl->d_items, items.size() * sizeof(int4));
+  if (ae != cudaSuccess) {
+    pl->d_items = nullptr;
+    return alloc_failed("work list", items.size() * sizeof(int4), ae);
+  }
   XE_CHECK(h, cudaMemcpy(pl->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
   pl->nitems = static_cast<int32_t>(items.size());
   pl->nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
@@ -334,14 +346,14 @@ corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
   } else {
     e = cudaMalloc(&h->acc, acc_bytes);
     if (e != cudaSuccess) {
-      fail(CORR_ENOMEM, "cudaMalloc(%zu bytes) for accumulators: %s", acc_bytes, cudaGetErrorString(e));
+      alloc_failed("cudaMalloc for accumulators", acc_bytes, e);
       h->acc = nullptr;
       ok = false;
     }
     h->own_acc = ok;
   }
-  if (ok && cudaMalloc(&h->d_err, sizeof(int32_t)) != cudaSuccess) {
-    fail(CORR_ENOMEM, "cudaMalloc error word failed");
+  if (ok && (e = cudaMalloc(&h->d_err, sizeof(int32_t))) != cudaSuccess) {
+    alloc_failed("cudaMalloc for the error word", sizeof(int32_t), e);
     ok = false;
   }
   if (ok && cudaMemset(h->d_err, 0, sizeof(int32_t)) != cudaSuccess) ok = !fail(CORR_ECUDA, "memset error word");
@@ -376,7 +388,10 @@ int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t s
       h->stage_bytes = 0;
     }
     cudaError_t e = cudaMalloc(&h->stage, need);
-    if (e != cudaSuccess) return fail(CORR_ENOMEM, "staging buffer (%zu bytes): %s", need, cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      h->stage = nullptr;
+      return alloc_failed("staging buffer", need, e);
+    }
     h->stage_bytes = need;
   }
   const int64_t rows = static_cast<int64_t>(T) * h->F;
@@ -446,9 +461,9 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
     b.h_desc = nullptr;
     b.d_desc = nullptr;
     const size_t cap = std::max<size_t>(frames, 64);
-    if (cudaMallocHost(&b.h_desc, cap * sizeof(xe::FrameDesc)) != cudaSuccess ||
-        cudaMalloc(&b.d_desc, cap * sizeof(xe::FrameDesc)) != cudaSuccess)
-      return fail(CORR_ENOMEM, "batch descriptor buffers (%zu frames)", cap);
+    cudaError_t e = cudaMallocHost(&b.h_desc, cap * sizeof(xe::FrameDesc));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_desc, cap * sizeof(xe::FrameDesc));
+    if (e != cudaSuccess) return alloc_failed("batch descriptor buffers", cap * sizeof(xe::FrameDesc), e);
     b.cap_frames = cap;
     if (b.exec) {
       cudaGraphExecDestroy(b.exec);
@@ -461,9 +476,9 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
     b.h_items = nullptr;
     b.d_items = nullptr;
     const size_t cap = std::max<size_t>(items + items / 4, 4096);
-    if (cudaMallocHost(&b.h_items, cap * sizeof(int4)) != cudaSuccess ||
-        cudaMalloc(&b.d_items, cap * sizeof(int4)) != cudaSuccess)
-      return fail(CORR_ENOMEM, "batch work-list buffers (%zu items)", cap);
+    cudaError_t e = cudaMallocHost(&b.h_items, cap * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_items, cap * sizeof(int4));
+    if (e != cudaSuccess) return alloc_failed("batch work-list buffers", cap * sizeof(int4), e);
     b.cap_items = cap;
     if (b.exec) {
       cudaGraphExecDestroy(b.exec);
@@ -606,6 +621,8 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
     d.fresh = h->fresh ? 1 : 0;
     d.B = h->B;
     d.vis = h->acc;
+    d.t0 = 0;
+    d.atomic = 0;
   }
   const int hybrid = hs[0]->product < 0 ? g_hybrid : hs[0]->product;
   if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
@@ -621,6 +638,131 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
     hs[k]->samples += Ts ? Ts[k] : hs[k]->T;
     ++hs[k]->launches;  // the handle's frame ran in one (shared) launch
     if ((rc = record_last(hs[k], st))) return rc;
+  }
+  return CORR_OK;
+}
+
+// ---- gated correlation: the samples of each gate add into that gate's handle ----
+// gate(t) = floor(((t + phase) mod period) * G / period) (Sec. IV: products
+// binned by time, for periodic signals). Every maximal run of samples in one
+// gate is a segment; a segment is a frame descriptor over the same input
+// whose samples outside [t0, t1) read as zero, adding atomically into its
+// gate's accumulators. The segments' tiles form one batched launch.
+int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T, int32_t period, int32_t phase,
+               void* stream) {
+  if (G < 1 || !gates || !in) return fail(CORR_EINVAL, "gated: bad arguments");
+  if (T < 1 || period < 1 || phase < 0 || phase >= period)
+    return fail(CORR_EINVAL, "gated: need T >= 1, period >= 1, 0 <= phase < period");
+  for (int g = 0; g < G; ++g) {
+    int rc = check_handle(gates[g]);
+    if (rc) return rc;
+    if (gates[g]->N != gates[0]->N || gates[g]->F != gates[0]->F || gates[g]->device != gates[0]->device)
+      return fail(CORR_EINVAL, "gated: gate handles must share N, F and the device");
+    for (int j = 0; j < g; ++j)
+      if (gates[j] == gates[g]) return fail(CORR_EINVAL, "gated: gate handles must be distinct");
+  }
+  corr_handle* h0 = gates[0];
+  // segments, found from the gate boundaries within a period
+  struct Seg {
+    int32_t t0, t1, g;
+  };
+  std::vector<Seg> segs;
+  std::vector<int64_t> per_gate(G, 0);
+  for (int64_t t = 0; t < T;) {
+    const int64_t pos = (t + phase) % period;
+    const int64_t g = pos * G / period;
+    const int64_t next = std::min<int64_t>(period, ceil_div((g + 1) * period, G));  // first position of gate g+1
+    const int64_t t1 = std::min<int64_t>(T, t + (next - pos));
+    segs.push_back({static_cast<int32_t>(t), static_cast<int32_t>(t1), static_cast<int32_t>(g)});
+    per_gate[g] += t1 - t;
+    t = t1;
+    if (static_cast<int64_t>(segs.size()) > kMaxBatchFrames)
+      return fail(CORR_EINVAL, "gated: more than %d gate segments in one frame (shorten T or lengthen the period)",
+                  kMaxBatchFrames);
+  }
+  for (int g = 0; g < G; ++g)
+    if (gates[g]->samples + per_gate[g] > CORR_MAX_SAMPLES)
+      return fail(CORR_EOVERFLOW, "gated: gate %d would exceed %d samples since its reset", g, CORR_MAX_SAMPLES);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  for (int g = 0; g < G; ++g)
+    if ((rc = order_after_last(gates[g], st))) return rc;
+  const uint8_t* frame;
+  int32_t np;
+  if ((rc = stage_if_needed(h0, in, T, st, &frame, &np))) return rc;
+  CUtensorMap map;
+  if ((rc = make_tmap(&map, frame, np, h0->F, T))) return rc;
+  // segments add atomically: fresh gates start from zero
+  for (int g = 0; g < G; ++g)
+    if (gates[g]->fresh) {
+      XE_CHECK(gates[g], cudaMemsetAsync(gates[g]->acc, 0, static_cast<size_t>(h0->F) * h0->B * 2 * sizeof(int32_t), st));
+      gates[g]->fresh = false;
+    }
+  std::vector<int32_t> bi, bj;
+  triangle_tiles(h0->N, xe::kTile, bi, bj);
+  struct It {
+    int4 w;
+    double cost;
+  };
+  std::vector<It> work;
+  for (size_t s = 0; s < segs.size(); ++s) {
+    const int32_t c0 = segs[s].t0 / xe::kTC, c1 = static_cast<int32_t>(ceil_div(segs[s].t1, xe::kTC));
+    for (int32_t f = 0; f < h0->F; ++f)
+      for (size_t u = 0; u < bi.size(); ++u)
+        work.push_back({make_int4(f | (static_cast<int32_t>(s) << 20), bi[u] | (bj[u] << 16), c0, c1),
+                        (bi[u] == bj[u] ? kDiagCost : 1.0) * (c1 - c0)});
+  }
+  std::stable_sort(work.begin(), work.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+  const int dev = h0->device;
+  const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
+  const int64_t nitems = static_cast<int64_t>(work.size());
+  const int64_t grid = std::min<int64_t>(slots, nitems);
+  const int64_t nseg = static_cast<int64_t>(segs.size());
+  if (h0->F >= (1 << 20)) return fail(CORR_EINVAL, "gated: F must be < 2^20");
+
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (!g_batch[dev]) g_batch[dev] = new (std::nothrow) BatchCtx;
+  if (!g_batch[dev]) return fail(CORR_ENOMEM, "batch context");
+  BatchCtx& ctx = *g_batch[dev];
+  BatchSet& b = ctx.set[ctx.next];
+  if (b.pending) {
+    cudaError_t e = cudaEventSynchronize(b.done);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "waiting for a previous batch: %s", cudaGetErrorString(e));
+    b.pending = false;
+  }
+  if ((rc = grow_set(b, static_cast<size_t>(nseg), static_cast<size_t>(nitems)))) return rc;
+  for (int64_t i = 0; i < nitems; ++i) {  // snake layout over the CTAs, as for batches
+    const int64_t r = i / grid, c = i % grid;
+    const int64_t pos = r * grid + ((r & 1) ? grid - 1 - c : c);
+    b.h_items[pos < nitems ? pos : i] = work[i].w;
+  }
+  if (nitems % grid != 0 && ((nitems / grid) & 1))
+    for (int64_t i = (nitems / grid) * grid; i < nitems; ++i) b.h_items[i] = work[i].w;
+  for (int64_t s = 0; s < nseg; ++s) {
+    xe::FrameDesc& d = b.h_desc[s];
+    d.map = map;
+    d.N = h0->N;
+    d.T = segs[s].t1;
+    d.nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
+    d.fresh = 0;
+    d.B = h0->B;
+    d.vis = gates[segs[s].g]->acc;
+    d.t0 = segs[s].t0;
+    d.atomic = 1;
+  }
+  const int hybrid = h0->product < 0 ? g_hybrid : h0->product;
+  if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
+      b.key_err != h0->d_err)
+    if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid))) return rc;
+  cudaError_t e = cudaGraphLaunch(b.exec, st);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
+  b.pending = true;
+  ctx.next ^= 1;
+  for (int g = 0; g < G; ++g) {
+    gates[g]->samples += per_gate[g];
+    ++gates[g]->launches;
+    if ((rc = record_last(gates[g], st))) return rc;
   }
   return CORR_OK;
 }
@@ -674,7 +816,10 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
     const size_t bytes = static_cast<size_t>(cT) * h->F * Np;
     for (int k = 0; k < 2; ++k) {
       cudaError_t e = cudaMalloc(&h->hchunk[k], bytes);
-      if (e != cudaSuccess) return fail(CORR_ENOMEM, "host-path chunk buffer: %s", cudaGetErrorString(e));
+      if (e != cudaSuccess) {
+        h->hchunk[k] = nullptr;
+        return alloc_failed("host-path chunk buffer", bytes, e);
+      }
       XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
       XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_used[k], cudaEventDisableTiming));
     }
@@ -759,6 +904,33 @@ int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs
 int corr_accumulate_batch_ex(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
                              void* stream) {
   return batch_impl(hs, inputs, Ts, n, stream);
+}
+
+int corr_accumulate_gated(corr_handle_t* const* gates, int G, const uint8_t* packed_dev, int32_t T, int32_t period,
+                          int32_t phase, void* stream) {
+  return gated_impl(gates, G, packed_dev, T, period, phase, stream);
+}
+
+int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t F, int32_t T, const int32_t* lags_dev,
+                    void* stream) {
+  if (!in_dev || !out_dev || !lags_dev) return fail(CORR_EINVAL, "shift_lags: NULL pointer");
+  if (in_dev == out_dev) return fail(CORR_EINVAL, "shift_lags: the output must not be the input");
+  if (N < 1 || N > CORR_MAX_N || F < 1 || T < 1) return fail(CORR_EINVAL, "shift_lags: bad N, F or T");
+  if (N % 4 == 0 && (reinterpret_cast<uintptr_t>(out_dev) & 3))
+    return fail(CORR_EINVAL, "shift_lags: output must be 4-byte aligned");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  int rc = device_setup(dev);
+  if (rc) return rc;
+  const int64_t total = static_cast<int64_t>(T) * F * ((N + 3) / 4);
+  const int threads = 256;
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, threads), int64_t(g_sms[dev]) * 16));
+  xe::shift_lags_kernel<<<static_cast<int>(blocks), threads, 0, static_cast<cudaStream_t>(stream)>>>(in_dev, out_dev,
+                                                                                                  N, F, T, lags_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "shift_lags launch: %s", cudaGetErrorString(e));
+  return CORR_OK;
 }
 
 int corr_set_option(corr_handle_t* h, int option, int64_t value) {
