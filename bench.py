@@ -38,7 +38,7 @@ WORKLOADS = {
     "pathfinder": ("PATHFINDER", "Pathfinder shape N=256 F=256 T=16384, Gaussian sigma=2.5 levels, one frame per launch"),
     "large_n": ("LARGE_N", "large N: N=8192 F=4 T=2048, sigma=2.5 plus a common tone, one frame per launch"),
 }
-EXTRA_WORKLOADS = ("batched", "served")
+EXTRA_WORKLOADS = ("batched", "served", "lags_gates")
 KERNEL_NAME = "corr_tile_kernel"
 KERNEL_SOURCES = ["paper_1503_06203_gb300/csrc/xe_corr.cuh", "paper_1503_06203_gb300/csrc/xe_ptx.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "corr_tile_kernel_pathfinder.md")
@@ -492,9 +492,71 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lags_gates(args):
+    """Sec. IV extensions on the Pathfinder frame: lag-shift bandwidth, gated vs plain correlation."""
+    import numpy as np
+    import torch
+
+    import paper_1503_06203_gb300 as xe
+    import synth
+    xe.build()
+    fr = synth.PATHFINDER
+    N, F, T = fr.N, fr.F, fr.T
+    x = torch.from_numpy(fr.make()).cuda()
+    lags = torch.from_numpy(np.random.default_rng(7).integers(-64, 64, N).astype(np.int32)).cuda()
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_shift = timed(lambda: xe.shift_lags(x, lags, out=y), 20)
+    gbs = 2.0 * N * F * T / ms_shift / 1e6
+    hbm = (measured_peaks_file() or {}).get("hbm_gbs", 6699.8)
+    G, period = 8, 1024
+    gates = [xe.Correlator(N, F, T) for _ in range(G)]
+    plain = xe.Correlator(N, F, T)
+
+    def gated_step():
+        for c in gates:
+            c.reset()
+        xe.accumulate_gated(gates, x, period, 0)
+
+    def plain_step():
+        plain.reset()
+        plain.accumulate(x)
+
+    ms_gated = timed(gated_step, 10)
+    ms_plain = timed(plain_step, 10)
+    ops = 4.0 * N * (N + 1) * F * T
+    line = {"metric": "lag shift GB/s and gated-correlation effective TOPS", "value": round(ops / ms_gated / 1e9, 3),
+            "unit": "TOPS", "n_gpus": 1, "higher_is_better": True, "dtype": "s8 x s8 -> s32",
+            "data": "synthetic (seeded generator, paper's shapes)",
+            "config": {"workload": "Pathfinder frame N=256 F=256 T=16384; lags uniform in [-64, 64); "
+                                   f"{G} gates of a {period}-sample period"},
+            "lag_shift": {"ms": round(ms_shift, 4), "gbs": round(gbs, 1), "hbm_peak_gbs": hbm,
+                          "frac": round(gbs / hbm, 4), "bound": "hbm",
+                          "algorithmic_bytes": 2 * N * F * T},
+            "gated": {"ms": round(ms_gated, 4), "effective_tops": round(ops / ms_gated / 1e9, 3), "gates": G,
+                      "segments": T // (period // G)},
+            "plain": {"ms": round(ms_plain, 4), "effective_tops": round(ops / ms_plain / 1e9, 3)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.workload == "batched":
+    if args.workload == "lags_gates":
+        run_lags_gates(args)
+    elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "served":
         run_served(args)

@@ -47,7 +47,7 @@ enum : int { kErrTimeoutFull = 1, kErrTimeoutEmpty = 2 };
 enum : int { kPxr = 0, kPxi = 1, kPsd = 2 };
 
 // One frame of a batched launch (device memory; the TMA descriptor first, 64-byte aligned).
-struct __align__(64) FrameDesc {
+struct FrameDesc {  // (aligned as its CUtensorMap)
   CUtensorMap map;   // [T][F][Np] bytes of the frame
   int32_t N, T, nch, fresh;
   int64_t B;         // N(N+1)/2
@@ -57,8 +57,9 @@ struct __align__(64) FrameDesc {
 };
 
 struct CorrArgs {
-  // {band f (| frame << 20 in a batch), bi | bj << 16, first chunk, end chunk};
-  // CTA k takes items k, k + grid, ...
+  // {band f (| frame << 20 in a batch), bi | bj << 16 (| 1 << 31: hold the sums
+  //  for this CTA's next item instead of writing them), first chunk, end chunk};
+  //  CTA k takes items k, k + grid, ...
   const int4* items;
   const FrameDesc* frames = nullptr;  // batch: per-frame descriptors; nullptr: the one frame described below
   int32_t nitems;
@@ -310,60 +311,54 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // at the same time work on the tiles of one band over the same time chunks
 // and share that band's input in L2.
 //
-// Warp roles. Warps 0-15: product and writer, 4 x 4 warps of 16 x 16 pieces
-// (three int32 accumulator sets, 24 registers a thread); four of them share
-// each SM sub-partition. Warps 16-19: unpack; lane 0 of warp 16 also issues
-// the TMA loads. One CTA per SM.
+// Warp roles. Warps 0-15 (warpgroups 0-3): product and writer, 4 x 4 warps
+// of 16 x 16 pieces (three int32 accumulator sets, 24 registers a thread);
+// four of them share each SM sub-partition. Warps 16-19 (warpgroup 4):
+// unpack; lane 0 of warp 16 also issues the TMA loads. One CTA per SM.
+
 // Walks (item, chunk) pairs of this CTA in order. T and nch are the current
 // item's frame's (from its descriptor in a batch, else from args); the writer
 // reads the rest when it needs it.
 struct Walk {
   int item, c, f, bi, bj, c1, frame, T, nch, T0;
-  const int4* items;
-  const FrameDesc* frames;
-  int nitems, stride;
-  __device__ __forceinline__ void load() {
-    if (item < nitems) {
-      const int4 w = items[item];
+  __device__ __forceinline__ void load(const CorrArgs& a) {
+    if (item < a.nitems) {
+      const int4 w = a.items[item];
       bi = w.y & 0xFFFF;
-      bj = w.y >> 16;
+      bj = (w.y >> 16) & 0x7FFF;  // (bit 31: hold, read by the writer)
       c = w.z;
       c1 = w.w;
-      if (frames) {
+      if (a.frames) {
         f = w.x & 0xFFFFF;
         const int fr = w.x >> 20;
         if (fr != frame) {
           frame = fr;
-          T = frames[fr].T;
-          nch = frames[fr].nch;
-          T0 = frames[fr].t0;
+          T = a.frames[fr].T;
+          nch = a.frames[fr].nch;
+          T0 = a.frames[fr].t0;
         }
       } else {
         f = w.x;
       }
     }
   }
-  __device__ __forceinline__ void start(const CorrArgs& a, int first, int step) {
-    items = a.items;
-    frames = a.frames;
-    nitems = a.nitems;
-    stride = step;
-    item = first;
+  __device__ __forceinline__ void start(const CorrArgs& a) {
+    item = blockIdx.x;
     frame = -1;
     T = a.T;
     nch = a.nch;
     T0 = 0;
-    load();
+    load(a);
   }
-  __device__ __forceinline__ bool valid() const { return item < nitems; }
-  __device__ __forceinline__ void next() {
+  __device__ __forceinline__ bool valid(const CorrArgs& a) const { return item < a.nitems; }
+  __device__ __forceinline__ void next(const CorrArgs& a) {
     if (++c == c1) {
-      item += stride;
-      load();
+      item += gridDim.x;
+      load(a);
     }
   }
-  __device__ __forceinline__ const CUtensorMap* map(const CUtensorMap* single) const {
-    return frames ? &frames[frame].map : single;
+  __device__ __forceinline__ const CUtensorMap* map(const CorrArgs& a, const CUtensorMap* single) const {
+    return a.frames ? &a.frames[frame].map : single;
   }
 };
 
@@ -393,13 +388,13 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const bool producer = uw == 0 && lane == 0;
     const int eg = lane & 15, p = lane >> 4, tg = 2 * uw + p;  // samples 16tg..16tg+15 of each chunk
     Walk ld;  // the TMA issuer walks the same units, kStages ahead
-    ld.start(args, blockIdx.x, gridDim.x);
+    ld.start(args);
     uint32_t issued = 0;
     const CUtensorMap* fenced = nullptr;
     auto issue = [&](void) {
       const int s = issued % kStages;
       const bool diag = ld.bi == ld.bj;
-      const CUtensorMap* map = ld.map(&tmap);
+      const CUtensorMap* map = ld.map(args, &tmap);
       if (args.frames && map != fenced) {  // a frame descriptor copied in before the launch
         tensormap_acquire(map);
         fenced = map;
@@ -408,16 +403,16 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       tma_load_3d(sm.box[s][0], map, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
       if (!diag) tma_load_3d(sm.box[s][1], map, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
       ++issued;
-      ld.next();
+      ld.next(args);
     };
     if (producer) {
       if (!args.frames) tma_prefetch_desc(&tmap);
-      for (int k = 0; k < kStages && ld.valid(); ++k) issue();
+      for (int k = 0; k < kStages && ld.valid(args); ++k) issue();
     }
     uint32_t it = 0;
     bool ok = true;
     Walk x;
-    for (x.start(args, blockIdx.x, gridDim.x); x.valid(); x.next(), ++it) {
+    for (x.start(args); x.valid(args); x.next(args), ++it) {
       const bool diag = x.bi == x.bj;
       const int s = it % kStages, buf = it % kPlaneBufs;
       // the plane buffer must be free (its previous chunk's products issued) and the box landed
@@ -444,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       }
       mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
       mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
-      if (producer && ld.valid()) {  // refill slot s once every unpack thread is done with it
+      if (producer && ld.valid(args)) {  // refill slot s once every unpack thread is done with it
         if (!mbar_wait_bounded(&sm.bempty[s], (it / kStages) & 1, kSpinLimit)) {
           atomicOr(args.err, kErrTimeoutEmpty);
           ok = false;
@@ -474,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   zero_acc(acc);
   uint32_t it = 0;
   Walk x;
-  for (x.start(args, blockIdx.x, gridDim.x); x.valid(); ++it) {
+  for (x.start(args); x.valid(args); ++it) {
     const bool diag = x.bi == x.bj;
     const int buf = it % kPlaneBufs;
     if (!mbar_wait_bounded(&sm.pfull[buf], (it / kPlaneBufs) & 1, kSpinLimit)) {
@@ -507,8 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
-    if (x.c + 1 == x.c1) {  // end of the item: write it
+    if (x.c + 1 == x.c1) {  // end of the item: write it, unless it holds its sums for the CTA's next item
       const int4 w = args.items[x.item];
+      if (w.y >= 0) {
       const bool whole = w.z == 0 && w.w == x.nch;
       const FrameDesc* d = args.frames ? &args.frames[x.frame] : nullptr;
       const int fresh = d ? d->fresh : args.fresh;
@@ -517,8 +513,9 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         write_piece(d ? d->N : args.N, d ? d->B : args.B, d ? d->vis : args.vis, x.f, x.bi * kTile, x.bj * kTile, pr,
                     pc, lane, mode, sel, acc);
       zero_acc(acc);
+      }
     }
-    x.next();
+    x.next(args);
   }
 }
 

@@ -5,43 +5,100 @@
 //   out[t][f][i] = in[t - lag_i][f][i]   if 0 <= t - lag_i < T
 //                = 0x88 (= 0 + 0i)       otherwise
 //
-// HBM-bound: every output byte is written once and every input byte read at
-// most once. A thread writes 4 consecutive elements of one (time, band) row
-// as one 32-bit word (warps write 128 contiguous bytes); it gathers the four
-// source bytes, which are contiguous when the lags are equal.
+// HBM-bound. A CTA shifts one band's block of 64 elements over kLagTB output
+// samples: it stages the source rows those elements need (the time block
+// widened by the block's lag span) in shared memory with coalesced 16-byte
+// loads, then writes each output row of 64 bytes as 32-bit words. A block
+// whose lags span more than kLagHalo samples gathers bytes from global memory
+// instead.
 #pragma once
 #include <cstdint>
 
 namespace xe {
 
-__global__ void shift_lags_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, int32_t N, int32_t F,
-                                  int32_t T, const int32_t* __restrict__ lags) {
-  const int64_t rows = static_cast<int64_t>(T) * F;  // (t, f) rows of N bytes
-  const int32_t quads = (N + 3) / 4;
-  const int64_t total = rows * quads;
+constexpr int kLagTB = 256;    // output samples per CTA
+constexpr int kLagHalo = 256;  // largest lag span staged in shared memory
+constexpr int kLagThreads = 256;
+
+__global__ void __launch_bounds__(kLagThreads) shift_lags_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                                                                 int32_t N, int32_t F, int32_t T,
+                                                                 const int32_t* __restrict__ lags) {
+  __shared__ __align__(16) uint8_t stage[(kLagTB + kLagHalo) * 64];
+  __shared__ int32_t lag_s[64];
+  __shared__ int32_t span[2];
+  const int nblk = (N + 63) / 64;
+  const int64_t cta = blockIdx.x;
+  const int eb = static_cast<int>(cta % nblk);
+  const int64_t rest = cta / nblk;
+  const int f = static_cast<int>(rest % F);
+  const int64_t t0 = (rest / F) * kLagTB;
+  const int i0 = eb * 64;
+  const int ne = min(64, N - i0);
+  if (threadIdx.x == 0) {
+    span[0] = INT32_MAX;
+    span[1] = INT32_MIN;
+  }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int32_t l = threadIdx.x < ne ? lags[i0 + threadIdx.x] : 0;
+    lag_s[threadIdx.x] = l;
+    if (threadIdx.x < ne) {
+      atomicMin(&span[0], l);
+      atomicMax(&span[1], l);
+    }
+  }
+  __syncthreads();
+  const int32_t lmin = span[0], lmax = span[1];
+  const int64_t tb = min(static_cast<int64_t>(kLagTB), T - t0);  // output rows of this CTA
+  const int64_t row_stride = static_cast<int64_t>(F) * N;
+  const bool staged = static_cast<int64_t>(lmax) - lmin <= kLagHalo;
+  // source rows t0 - lmax .. t0 + tb - 1 - lmin, clipped to the frame
+  const int64_t s_lo = max(int64_t(0), t0 - lmax);
+  const int64_t s_hi = min(static_cast<int64_t>(T), t0 + tb - lmin);  // exclusive
+  if (staged && s_hi > s_lo) {
+    const bool vec = (N % 16 == 0) && ne == 64 && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+    const int64_t rows = s_hi - s_lo;
+    if (vec) {
+      for (int64_t k = threadIdx.x; k < rows * 4; k += kLagThreads) {
+        const int64_t r = k >> 2;
+        const int q = static_cast<int>(k & 3);
+        const uint4 v = *reinterpret_cast<const uint4*>(in + (s_lo + r) * row_stride + static_cast<int64_t>(f) * N + i0 + 16 * q);
+        *reinterpret_cast<uint4*>(stage + r * 64 + 16 * q) = v;
+      }
+    } else {
+      for (int64_t k = threadIdx.x; k < rows * 64; k += kLagThreads) {
+        const int64_t r = k >> 6;
+        const int e = static_cast<int>(k & 63);
+        stage[r * 64 + e] = e < ne ? in[(s_lo + r) * row_stride + static_cast<int64_t>(f) * N + i0 + e] : 0x88;
+      }
+    }
+  }
+  __syncthreads();
   const bool word_ok = (N % 4) == 0;
-  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
-       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t row = k / quads;
-    const int32_t i0 = static_cast<int32_t>(k - row * quads) * 4;
-    const int64_t t = row / F;
-    const int64_t f = row - t * F;
+  // each thread writes 4 consecutive elements of an output row
+  for (int k = threadIdx.x; k < tb * 16; k += kLagThreads) {
+    const int r = k >> 4;
+    const int e0 = (k & 15) * 4;
+    if (e0 >= ne) continue;
+    const int64_t t = t0 + r;
     uint32_t word = 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int32_t i = i0 + u;
+      const int e = e0 + u;
       uint32_t b = 0x88u;
-      if (i < N) {
-        const int64_t src = t - lags[i];
-        if (src >= 0 && src < T) b = in[(src * F + f) * N + i];
+      if (e < ne) {
+        const int64_t src = t - lag_s[e];
+        if (src >= 0 && src < T) {
+          b = staged ? stage[(src - s_lo) * 64 + e] : in[src * row_stride + static_cast<int64_t>(f) * N + i0 + e];
+        }
       }
       word |= b << (8 * u);
     }
-    uint8_t* dst = out + row * N + i0;
+    uint8_t* dst = out + t * row_stride + static_cast<int64_t>(f) * N + i0 + e0;
     if (word_ok) {
       *reinterpret_cast<uint32_t*>(dst) = word;
     } else {
-      for (int u = 0; u < 4 && i0 + u < N; ++u) dst[u] = static_cast<uint8_t>(word >> (8 * u));
+      for (int u = 0; u < 4 && e0 + u < ne; ++u) dst[u] = static_cast<uint8_t>(word >> (8 * u));
     }
   }
 }

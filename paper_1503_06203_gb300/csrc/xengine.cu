@@ -676,7 +676,7 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     segs.push_back({static_cast<int32_t>(t), static_cast<int32_t>(t1), static_cast<int32_t>(g)});
     per_gate[g] += t1 - t;
     t = t1;
-    if (static_cast<int64_t>(segs.size()) > kMaxBatchFrames)
+    if (static_cast<int64_t>(segs.size()) >= kMaxBatchFrames)  // (one descriptor is kept for padding)
       return fail(CORR_EINVAL, "gated: more than %d gate segments in one frame (shorten T or lengthen the period)",
                   kMaxBatchFrames);
   }
@@ -698,27 +698,58 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
       XE_CHECK(gates[g], cudaMemsetAsync(gates[g]->acc, 0, static_cast<size_t>(h0->F) * h0->B * 2 * sizeof(int32_t), st));
       gates[g]->fresh = false;
     }
+  // groups: one (band, tile, gate) with all its segments in time order, run by
+  // one CTA back to back ("hold" between them) and written once; groups are
+  // dealt to CTAs longest-first onto the least-loaded CTA
   std::vector<int32_t> bi, bj;
   triangle_tiles(h0->N, xe::kTile, bi, bj);
-  struct It {
-    int4 w;
+  std::vector<std::vector<int32_t>> gate_segs(G);
+  for (size_t s = 0; s < segs.size(); ++s) gate_segs[segs[s].g].push_back(static_cast<int32_t>(s));
+  struct Group {
+    int32_t f, tile, g;
     double cost;
   };
-  std::vector<It> work;
-  for (size_t s = 0; s < segs.size(); ++s) {
-    const int32_t c0 = segs[s].t0 / xe::kTC, c1 = static_cast<int32_t>(ceil_div(segs[s].t1, xe::kTC));
-    for (int32_t f = 0; f < h0->F; ++f)
-      for (size_t u = 0; u < bi.size(); ++u)
-        work.push_back({make_int4(f | (static_cast<int32_t>(s) << 20), bi[u] | (bj[u] << 16), c0, c1),
-                        (bi[u] == bj[u] ? kDiagCost : 1.0) * (c1 - c0)});
-  }
-  std::stable_sort(work.begin(), work.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+  std::vector<Group> groups;
+  for (int32_t f = 0; f < h0->F; ++f)
+    for (size_t u = 0; u < bi.size(); ++u)
+      for (int g = 0; g < G; ++g) {
+        if (gate_segs[g].empty()) continue;
+        double c = 0.0;
+        for (int32_t s : gate_segs[g]) c += ceil_div(segs[s].t1, xe::kTC) - segs[s].t0 / xe::kTC;
+        groups.push_back({f, static_cast<int32_t>(u), g, c * (bi[u] == bj[u] ? kDiagCost : 1.0)});
+      }
+  std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
   const int dev = h0->device;
   const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
-  const int64_t nitems = static_cast<int64_t>(work.size());
-  const int64_t grid = std::min<int64_t>(slots, nitems);
-  const int64_t nseg = static_cast<int64_t>(segs.size());
-  if (h0->F >= (1 << 20)) return fail(CORR_EINVAL, "gated: F must be < 2^20");
+  const int64_t grid = std::min<int64_t>(slots, static_cast<int64_t>(groups.size()));
+  std::vector<std::vector<int4>> column(static_cast<size_t>(grid));
+  {
+    std::vector<std::pair<double, int64_t>> heap;  // (load, cta), min-heap
+    for (int64_t c = 0; c < grid; ++c) heap.push_back({0.0, c});
+    auto cmp = [](const std::pair<double, int64_t>& a, const std::pair<double, int64_t>& b) { return a.first > b.first; };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (const Group& gr : groups) {
+      std::pop_heap(heap.begin(), heap.end(), cmp);
+      auto& slot = heap.back();
+      const auto& ss = gate_segs[gr.g];
+      for (size_t k = 0; k < ss.size(); ++k) {
+        const Seg& sg = segs[ss[k]];
+        const int32_t hold = k + 1 < ss.size() ? static_cast<int32_t>(0x80000000u) : 0;
+        column[slot.second].push_back(make_int4(gr.f | (ss[k] << 20), bi[gr.tile] | (bj[gr.tile] << 16) | hold,
+                                                sg.t0 / xe::kTC, static_cast<int32_t>(ceil_div(sg.t1, xe::kTC))));
+      }
+      slot.first += gr.cost;
+      std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+  }
+  size_t rows = 0;
+  for (const auto& col : column) rows = std::max(rows, col.size());
+  // CTA c's r-th item sits at r*grid + c. Shorter columns are padded with one-chunk
+  // items over an extra, empty segment (every sample masked), which add zeros.
+  const int64_t nitems = static_cast<int64_t>(rows) * grid;
+  const int64_t nseg = static_cast<int64_t>(segs.size()) + 1;
+  const int4 pad = make_int4(static_cast<int32_t>(segs.size()) << 20, 0, 0, 1);
+  if (nitems > INT32_MAX || h0->F >= (1 << 20)) return fail(CORR_EINVAL, "gated: work list too large");
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
   if (!g_batch[dev]) g_batch[dev] = new (std::nothrow) BatchCtx;
@@ -731,23 +762,19 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     b.pending = false;
   }
   if ((rc = grow_set(b, static_cast<size_t>(nseg), static_cast<size_t>(nitems)))) return rc;
-  for (int64_t i = 0; i < nitems; ++i) {  // snake layout over the CTAs, as for batches
-    const int64_t r = i / grid, c = i % grid;
-    const int64_t pos = r * grid + ((r & 1) ? grid - 1 - c : c);
-    b.h_items[pos < nitems ? pos : i] = work[i].w;
-  }
-  if (nitems % grid != 0 && ((nitems / grid) & 1))
-    for (int64_t i = (nitems / grid) * grid; i < nitems; ++i) b.h_items[i] = work[i].w;
+  for (int64_t c = 0; c < grid; ++c)
+    for (size_t r = 0; r < rows; ++r) b.h_items[r * grid + c] = r < column[c].size() ? column[c][r] : pad;
   for (int64_t s = 0; s < nseg; ++s) {
+    const bool empty = s == nseg - 1;
     xe::FrameDesc& d = b.h_desc[s];
     d.map = map;
     d.N = h0->N;
-    d.T = segs[s].t1;
+    d.T = empty ? 0 : segs[s].t1;
     d.nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
     d.fresh = 0;
     d.B = h0->B;
-    d.vis = gates[segs[s].g]->acc;
-    d.t0 = segs[s].t0;
+    d.vis = gates[empty ? 0 : segs[s].g]->acc;
+    d.t0 = empty ? 1 : segs[s].t0;  // t0 > T: nothing is valid
     d.atomic = 1;
   }
   const int hybrid = h0->product < 0 ? g_hybrid : h0->product;
@@ -923,11 +950,10 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   int rc = device_setup(dev);
   if (rc) return rc;
-  const int64_t total = static_cast<int64_t>(T) * F * ((N + 3) / 4);
-  const int threads = 256;
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, threads), int64_t(g_sms[dev]) * 16));
-  xe::shift_lags_kernel<<<static_cast<int>(blocks), threads, 0, static_cast<cudaStream_t>(stream)>>>(in_dev, out_dev,
-                                                                                                  N, F, T, lags_dev);
+  const int64_t ctas = static_cast<int64_t>(ceil_div(N, 64)) * F * ceil_div(T, xe::kLagTB);
+  if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");
+  xe::shift_lags_kernel<<<static_cast<unsigned>(ctas), xe::kLagThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+      in_dev, out_dev, N, F, T, lags_dev);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CORR_ECUDA, "shift_lags launch: %s", cudaGetErrorString(e));
   return CORR_OK;
