@@ -174,9 +174,13 @@ def shift_lags(x, lags, out=None, stream=None):
     x: CUDA uint8 [T][F][N]; lags: CUDA int32 [N]; returns `out` (allocated if None).
     """
     import torch
+    if not (x.is_cuda and x.dtype == torch.uint8 and x.dim() == 3 and x.is_contiguous()):
+        raise ValueError("x must be a contiguous CUDA uint8 tensor [T][F][N]")
     T, F, N = x.shape
     if out is None:
         out = torch.empty_like(x)
+    if not (out.is_cuda and out.dtype == torch.uint8 and out.shape == x.shape and out.is_contiguous()):
+        raise ValueError("out must be a contiguous CUDA uint8 tensor shaped like x")
     assert lags.is_cuda and lags.dtype == torch.int32 and lags.numel() == N and lags.is_contiguous()
     check(lib().corr_shift_lags(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), N, F, T,
                                 ctypes.c_void_p(lags.data_ptr()), _stream_ptr(stream)))

@@ -442,17 +442,7 @@ struct BatchCtx {
 };
 
 std::mutex g_batch_mu;
-BatchCtx* g_batch[64];
-
-void free_set(BatchSet& b) {
-  if (b.pending && b.done) cudaEventSynchronize(b.done);
-  if (b.exec) cudaGraphExecDestroy(b.exec);
-  if (b.h_desc) cudaFreeHost(b.h_desc);
-  if (b.h_items) cudaFreeHost(b.h_items);
-  if (b.d_desc) cudaFree(b.d_desc);
-  if (b.d_items) cudaFree(b.d_items);
-  b = BatchSet();
-}
+BatchCtx* g_batch[64];  // per device, kept for the life of the process
 
 int grow_set(BatchSet& b, size_t frames, size_t items) {
   if (frames > b.cap_frames) {
@@ -938,6 +928,38 @@ int corr_accumulate_gated(corr_handle_t* const* gates, int G, const uint8_t* pac
   return gated_impl(gates, G, packed_dev, T, period, phase, stream);
 }
 
+// Fault word of the streaming lag kernel: host-mapped, so the next call reads
+// it without a device synchronisation.
+std::mutex g_lag_mu;
+int32_t* g_lag_err_host = nullptr;
+int32_t* g_lag_err_dev = nullptr;
+int g_lag_ctas_per_sm[64] = {};
+
+int lag_stream_setup(int dev) {
+  std::lock_guard<std::mutex> lk(g_lag_mu);
+  if (!g_lag_err_host) {
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&g_lag_err_host), sizeof(int32_t), cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+      g_lag_err_host = nullptr;
+      return alloc_failed("shift_lags fault word", sizeof(int32_t), e);
+    }
+    *g_lag_err_host = 0;
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&g_lag_err_dev), g_lag_err_host, 0);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e));
+  }
+  if (!g_lag_ctas_per_sm[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(xe::shift_lags_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         xe::kLagStreamSmem);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::shift_lags_stream_kernel, xe::kLagStreamThreads,
+                                                      xe::kLagStreamSmem);
+    if (e != cudaSuccess || bps < 1) return fail(CORR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    g_lag_ctas_per_sm[dev] = bps;
+  }
+  return CORR_OK;
+}
+
 int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t F, int32_t T, const int32_t* lags_dev,
                     void* stream) {
   if (!in_dev || !out_dev || !lags_dev) return fail(CORR_EINVAL, "shift_lags: NULL pointer");
@@ -950,10 +972,35 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   int rc = device_setup(dev);
   if (rc) return rc;
-  const int64_t ctas = static_cast<int64_t>(ceil_div(N, 64)) * F * ceil_div(T, xe::kLagTB);
-  if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");
-  xe::shift_lags_kernel<<<static_cast<unsigned>(ctas), xe::kLagThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      in_dev, out_dev, N, F, T, lags_dev);
+  if (g_lag_err_host && *reinterpret_cast<volatile int32_t*>(g_lag_err_host)) {
+    *g_lag_err_host = 0;
+    return fail(CORR_ETIMEOUT, "an earlier shift_lags launch reported a device wait that ran out");
+  }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool streamable = N % 16 == 0 && (reinterpret_cast<uintptr_t>(in_dev) & 15) == 0 &&
+                          (reinterpret_cast<uintptr_t>(out_dev) & 15) == 0;
+  if (streamable) {
+    rc = lag_stream_setup(dev);
+    if (rc) return rc;
+    // segments of the time axis: about 8 waves of CTAs, each segment at least
+    // 1024 samples (its boundary re-reads the lag range once)
+    const int64_t units = ceil_div(N, 64) * F;
+    const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_lag_ctas_per_sm[dev];
+    const int64_t nseg_want = std::max<int64_t>(1, ceil_div(8 * slots, units));
+    int64_t tseg = ceil_div(ceil_div(T, nseg_want), 128) * 128;
+    tseg = std::max<int64_t>(tseg, std::min<int64_t>(ceil_div(T, 128) * 128, 1024));
+    const int64_t ctas = units * ceil_div(T, tseg);
+    if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");
+    CUtensorMap tm;
+    rc = make_tmap(&tm, in_dev, N, F, T);
+    if (rc) return rc;
+    xe::LagStreamArgs la{in_dev, out_dev, lags_dev, N, F, T, static_cast<int32_t>(tseg), g_lag_err_dev};
+    xe::shift_lags_stream_kernel<<<static_cast<unsigned>(ctas), xe::kLagStreamThreads, xe::kLagStreamSmem, st>>>(tm, la);
+  } else {
+    const int64_t ctas = ceil_div(N, 64) * F * ceil_div(T, xe::kLagTB);
+    if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");
+    xe::shift_lags_kernel<<<static_cast<unsigned>(ctas), xe::kLagThreads, 0, st>>>(in_dev, out_dev, N, F, T, lags_dev);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CORR_ECUDA, "shift_lags launch: %s", cudaGetErrorString(e));
   return CORR_OK;

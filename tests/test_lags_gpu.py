@@ -39,3 +39,63 @@ def test_shift_then_correlate(xe):
         c.accumulate(y)
         V = c.readout().cpu().numpy()
     assert np.array_equal(V.astype(np.int64), oracle.visibilities(oracle.shift_lags(x, lags)))
+
+
+def _lag_case(kind, N, T, rng):
+    if kind == "uniform100":
+        return rng.integers(-100, 100, N)
+    if kind == "span_limit":  # block 0 spans exactly the ring's 512 samples, block 1 one more
+        lags = rng.integers(-200, 200, N)
+        lags[0], lags[1] = -256, 256
+        if N > 65:
+            lags[64], lags[65] = -257, 256
+        return lags
+    if kind == "const_pos":
+        return np.full(N, 300)
+    if kind == "beyond_pos":
+        return np.full(N, T + 100)
+    if kind == "beyond_neg":
+        return np.full(N, -(T + 100))
+    if kind == "small":
+        return rng.integers(-3, 4, N)
+    if kind == "extreme":  # int32 ends: every such element is empty
+        lags = rng.integers(-50, 50, N)
+        lags[::7] = np.iinfo(np.int32).min
+        lags[3::7] = np.iinfo(np.int32).max
+        return lags
+    raise ValueError(kind)
+
+
+# Streaming (TMA ring) path: N % 16 == 0 and 16-byte aligned buffers. The cases
+# cover a ragged element block (N = 80), ragged T, several time segments
+# (T = 8192), the ring's lag-range limit and one past it, constant lags,
+# elements shifted out entirely and the int32 ends of the lag range.
+@pytest.mark.parametrize("N,F,T,kind", [
+    (80, 3, 1000, "uniform100"),
+    (128, 2, 3000, "span_limit"),
+    (64, 1, 5000, "const_pos"),
+    (64, 2, 700, "beyond_pos"),
+    (64, 2, 700, "beyond_neg"),
+    (256, 8, 8192, "uniform100"),
+    (16, 1, 129, "small"),
+    (96, 2, 2500, "extreme"),
+])
+def test_shift_streaming_matches_oracle(xe, N, F, T, kind):
+    import torch
+    x = synth.gauss(N, F, T, 2.5, 70 + N + T)
+    lags = _lag_case(kind, N, T, np.random.default_rng(N * 31 + T)).astype(np.int32)
+    y = xe.shift_lags(torch.from_numpy(x).cuda(), torch.from_numpy(lags).cuda())
+    assert np.array_equal(y.cpu().numpy(), oracle.shift_lags(x, lags))
+
+
+def test_shift_unaligned_input(xe):
+    """An input starting one byte past an aligned address takes the staged kernel; same result."""
+    import torch
+    N, F, T = 64, 2, 1500
+    x = synth.gauss(N, F, T, 2.5, 91)
+    lags = np.random.default_rng(5).integers(-90, 90, N).astype(np.int32)
+    buf = torch.empty(x.size + 1, dtype=torch.uint8, device="cuda")
+    xin = buf[1:].view(T, F, N)
+    xin.copy_(torch.from_numpy(x))
+    y = xe.shift_lags(xin, torch.from_numpy(lags).cuda())
+    assert np.array_equal(y.cpu().numpy(), oracle.shift_lags(x, lags))
