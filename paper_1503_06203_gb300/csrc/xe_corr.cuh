@@ -319,49 +319,59 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // Walks (item, chunk) pairs of this CTA in order. T and nch are the current
 // item's frame's (from its descriptor in a batch, else from args); the writer
 // reads the rest when it needs it.
+template <bool kFrames>
 struct Walk {
   int item, c, f, bi, bj, c1, frame, T, nch, T0;
-  __device__ __forceinline__ void load(const CorrArgs& a) {
-    if (item < a.nitems) {
-      const int4 w = a.items[item];
+  const int4* items;
+  const FrameDesc* frames;
+  int nitems, stride;
+  __device__ __forceinline__ void load() {
+    if (item < nitems) {
+      const int4 w = items[item];
       bi = w.y & 0xFFFF;
-      bj = (w.y >> 16) & 0x7FFF;  // (bit 31: hold, read by the writer)
       c = w.z;
       c1 = w.w;
-      if (a.frames) {
+      if (kFrames) {
+        bj = (w.y >> 16) & 0x7FFF;  // (bit 31: hold, read by the writer)
         f = w.x & 0xFFFFF;
         const int fr = w.x >> 20;
         if (fr != frame) {
           frame = fr;
-          T = a.frames[fr].T;
-          nch = a.frames[fr].nch;
-          T0 = a.frames[fr].t0;
+          T = frames[fr].T;
+          nch = frames[fr].nch;
+          T0 = frames[fr].t0;
         }
       } else {
+        bj = w.y >> 16;
         f = w.x;
       }
     }
   }
   __device__ __forceinline__ void start(const CorrArgs& a) {
+    items = a.items;
+    frames = a.frames;
+    nitems = a.nitems;
+    stride = gridDim.x;
     item = blockIdx.x;
     frame = -1;
     T = a.T;
     nch = a.nch;
     T0 = 0;
-    load(a);
+    load();
   }
-  __device__ __forceinline__ bool valid(const CorrArgs& a) const { return item < a.nitems; }
-  __device__ __forceinline__ void next(const CorrArgs& a) {
+  __device__ __forceinline__ bool valid() const { return item < nitems; }
+  __device__ __forceinline__ void next() {
     if (++c == c1) {
-      item += gridDim.x;
-      load(a);
+      item += stride;
+      load();
     }
   }
-  __device__ __forceinline__ const CUtensorMap* map(const CorrArgs& a, const CUtensorMap* single) const {
-    return a.frames ? &a.frames[frame].map : single;
+  __device__ __forceinline__ const CUtensorMap* map(const CUtensorMap* single) const {
+    return kFrames ? &frames[frame].map : single;
   }
 };
 
+template <bool kFrames>
 __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 CorrArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -387,15 +397,15 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const int uw = warp - kMmaWarps;  // 0..3
     const bool producer = uw == 0 && lane == 0;
     const int eg = lane & 15, p = lane >> 4, tg = 2 * uw + p;  // samples 16tg..16tg+15 of each chunk
-    Walk ld;  // the TMA issuer walks the same units, kStages ahead
+    Walk<kFrames> ld;  // the TMA issuer walks the same units, kStages ahead
     ld.start(args);
     uint32_t issued = 0;
     const CUtensorMap* fenced = nullptr;
     auto issue = [&](void) {
       const int s = issued % kStages;
       const bool diag = ld.bi == ld.bj;
-      const CUtensorMap* map = ld.map(args, &tmap);
-      if (args.frames && map != fenced) {  // a frame descriptor copied in before the launch
+      const CUtensorMap* map = ld.map(&tmap);
+      if (kFrames && map != fenced) {  // a frame descriptor copied in before the launch
         tensormap_acquire(map);
         fenced = map;
       }
@@ -403,16 +413,16 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       tma_load_3d(sm.box[s][0], map, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
       if (!diag) tma_load_3d(sm.box[s][1], map, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
       ++issued;
-      ld.next(args);
+      ld.next();
     };
     if (producer) {
-      if (!args.frames) tma_prefetch_desc(&tmap);
-      for (int k = 0; k < kStages && ld.valid(args); ++k) issue();
+      if (!kFrames) tma_prefetch_desc(&tmap);
+      for (int k = 0; k < kStages && ld.valid(); ++k) issue();
     }
     uint32_t it = 0;
     bool ok = true;
-    Walk x;
-    for (x.start(args); x.valid(args); x.next(args), ++it) {
+    Walk<kFrames> x;
+    for (x.start(args); x.valid(); x.next(), ++it) {
       const bool diag = x.bi == x.bj;
       const int s = it % kStages, buf = it % kPlaneBufs;
       // the plane buffer must be free (its previous chunk's products issued) and the box landed
@@ -439,7 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       }
       mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
       mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
-      if (producer && ld.valid(args)) {  // refill slot s once every unpack thread is done with it
+      if (producer && ld.valid()) {  // refill slot s once every unpack thread is done with it
         if (!mbar_wait_bounded(&sm.bempty[s], (it / kStages) & 1, kSpinLimit)) {
           atomicOr(args.err, kErrTimeoutEmpty);
           ok = false;
@@ -468,8 +478,8 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   int32_t acc[3][2][4];
   zero_acc(acc);
   uint32_t it = 0;
-  Walk x;
-  for (x.start(args); x.valid(args); ++it) {
+  Walk<kFrames> x;
+  for (x.start(args); x.valid(); ++it) {
     const bool diag = x.bi == x.bj;
     const int buf = it % kPlaneBufs;
     if (!mbar_wait_bounded(&sm.pfull[buf], (it / kPlaneBufs) & 1, kSpinLimit)) {
@@ -504,9 +514,9 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
     if (x.c + 1 == x.c1) {  // end of the item: write it, unless it holds its sums for the CTA's next item
       const int4 w = args.items[x.item];
-      if (w.y >= 0) {
+      if (!kFrames || w.y >= 0) {
       const bool whole = w.z == 0 && w.w == x.nch;
-      const FrameDesc* d = args.frames ? &args.frames[x.frame] : nullptr;
+      const FrameDesc* d = kFrames ? &args.frames[x.frame] : nullptr;
       const int fresh = d ? d->fresh : args.fresh;
       const int mode = (d && d->atomic) ? 2 : (whole ? (fresh ? 0 : 1) : 2);
       if (sel != kSelIdle)
@@ -515,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       zero_acc(acc);
       }
     }
-    x.next(args);
+    x.next();
   }
 }
 

@@ -59,11 +59,14 @@ int device_setup(int dev) {
   std::lock_guard<std::mutex> lk(g_dev_mu);
   if (dev < 0 || dev >= 64) return fail(CORR_EINVAL, "device ordinal %d out of range", dev);
   if (g_dev_ready[dev]) return CORR_OK;
-  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(xe::corr_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel, xe::kThreads, kSmemBytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel<false>, xe::kThreads, kSmemBytes);
   if (e != cudaSuccess || bps < 1)
     return fail(CORR_ECUDA, "occupancy query: %s (blocks/SM %d)", cudaGetErrorString(e), bps);
   int sms = 0;
@@ -310,7 +313,7 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.fresh = h->fresh ? 1 : 0;
   a.hybrid = h->product < 0 ? g_hybrid : h->product;
   a.err = h->d_err;
-  xe::corr_tile_kernel<<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  xe::corr_tile_kernel<false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
   ++h->launches;
   h->fresh = false;
@@ -511,7 +514,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel);
+  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel<true>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -1260,7 +1263,7 @@ extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int3
   a.hybrid = 0;
   a.err = reinterpret_cast<int32_t*>(scratch);
   const int grid = static_cast<int>(std::min<int64_t>(slots, nitems));
-  xe::corr_tile_kernel<<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  xe::corr_tile_kernel<false><<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(CORR_ECUDA, "noalloc correlate: %s", cudaGetErrorString(e));
   if (status_dev && (e = cudaMemcpyAsync(status_dev, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) !=
                         cudaSuccess)
