@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--served-frames", type=int, default=160, help="served: frames per rate")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch knobs (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -118,8 +119,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def recorded_traffic(workload: str, product: int, split: int):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source
+    with the same launch knobs (a time split changes the writers' traffic)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     vals = {}
@@ -129,6 +131,8 @@ def recorded_traffic(workload: str):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256_16") != kernel_source_hash() or vals.get("workload") != workload:
+        return None
+    if vals.get("options") != f"product={product} split={split}":
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -290,7 +294,8 @@ def run_xengine(args, wl_key):
 
     c = xe.Correlator(N, F, T)
     from paper_1503_06203_gb300 import autotune
-    tuned = autotune.apply(c)  # knobs for this shape on this GPU (tuned once, outside the timed region)
+    # knobs for this shape on this GPU (tuned once, outside the timed region)
+    tuned = {"note": "library defaults"} if args.no_tune else autotune.apply(c)
     sampler = ClockSampler(local).start()
     for _ in range(args.warmup):
         c.reset()
@@ -363,7 +368,7 @@ def run_xengine(args, wl_key):
     peak = (combo if hybrid else imma) / 1e12
     hw_ops = hardware_ops(N, F, T)
     hw_tops = hw_ops / (avg_kernel_ms * 1e-3) / 1e12
-    traffic = recorded_traffic(wl_key)
+    traffic = recorded_traffic(wl_key, c.get_option(xe.CORR_OPT_PRODUCT), c.get_option(xe.CORR_OPT_SPLIT))
     line = {
         "metric": "Effective TOPS", "value": round(value, 3), "unit": "TOPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),

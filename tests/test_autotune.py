@@ -15,6 +15,15 @@ def test_cache_roundtrip_and_candidates(tmp_path):
     assert all(s <= 1 for _, s in autotune.candidates(128))  # one chunk: no splits beyond 1
 
 
+def test_pick_keeps_default_within_margin():
+    from paper_1503_06203_gb300 import autotune
+    trials = [{"product": 1, "split": 0, "ms": 5.30}, {"product": 1, "split": 2, "ms": 5.28},
+              {"product": 0, "split": 0, "ms": 6.0}]
+    assert autotune.pick(trials) is trials[0]  # 0.4% faster: within the margin
+    trials[1]["ms"] = 5.0
+    assert autotune.pick(trials) is trials[1]  # 5.7% faster: taken
+
+
 @pytest.mark.gpu
 def test_every_knob_is_bit_exact_and_tuning_caches(tmp_path):
     import torch
