@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch knobs (profiling runs)")
+    ap.add_argument("--product", type=int, choices=[0, 1, 2], default=None,
+                    help="force the product path (0 tensor cores, 1 tensor cores + dp4a, 2 offset-encoded operands)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -296,6 +298,9 @@ def run_xengine(args, wl_key):
     from paper_1503_06203_gb300 import autotune
     # knobs for this shape on this GPU (tuned once, outside the timed region)
     tuned = {"note": "library defaults"} if args.no_tune else autotune.apply(c)
+    if args.product is not None:
+        c.set_option(xe.CORR_OPT_PRODUCT, args.product)
+        tuned = dict(tuned or {}, product=args.product, forced=True)
     sampler = ClockSampler(local).start()
     for _ in range(args.warmup):
         c.reset()
@@ -363,7 +368,8 @@ def run_xengine(args, wl_key):
         cpu = {"value": round(v, 6), "unit": "TOPS", "cores": cores, "kind": "oracle", "sample": desc}
 
     achieved = ops / (avg_kernel_ms * 1e-3) / 1e12
-    hybrid = c.get_option(xe.CORR_OPT_PRODUCT) == 1
+    product = c.get_option(xe.CORR_OPT_PRODUCT)
+    hybrid = product != 0  # paths 1 and 2 both run tensor cores and dp4a side by side
     # the kernel's pipes: tensor cores and dp4a side by side (default), or tensor cores alone
     peak = (combo if hybrid else imma) / 1e12
     hw_ops = hardware_ops(N, F, T)
@@ -384,7 +390,8 @@ def run_xengine(args, wl_key):
                      "peak_source": ("measured in this run, all SMs, register-resident operands: "
                                      + ("mma.sync m16n8k32 s8 and dp4a issued together (best of 16/24/32 dp4a per MMA)"
                                         if hybrid else "mma.sync m16n8k32 s8")),
-                     "product_path": "tensor cores + dp4a" if hybrid else "tensor cores",
+                     "product_path": {0: "tensor cores", 1: "tensor cores + dp4a",
+                                      2: "tensor cores + dp4a on offset-encoded operands (Eq. 3 route)"}[product],
                      "note": "achieved counts Eq. 2 operations (8 per complex MAC); the kernel's three-product form "
                              "executes 6 integer operations per complex MAC, so achieved/peak can reach 4/3; "
                              "hw_frac compares the executed operations with the peak",

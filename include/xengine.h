@@ -148,8 +148,13 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
  * corr_set_option -- per-handle launch knobs (the autotuner's controls; the
  * results do not depend on them):
  *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores for
- *     the first 96 of each 128-sample chunk and dp4a for the last 32, -1 = the
- *     library default (1 unless the XE_PRODUCT=mma environment variable is set).
+ *     the first 96 of each 128-sample chunk and dp4a for the last 32, 2 = as 1
+ *     on the offset-encoded nibbles (unsigned operands, Sec. III.A's route):
+ *     two extra kernels per call sum each element's nibbles over time and
+ *     seed the output with the Eq. 3 offset terms (restated for the
+ *     three-product form), and the correlator adds onto them; -1 = the
+ *     library default (1 unless the XE_PRODUCT=mma environment variable is
+ *     set). Batched and gated launches treat 2 as 1.
  *   CORR_OPT_SPLIT: 0 = automatic time split, k >= 1 = cut the time axis into
  *     k ranges (atomic adds when k > 1).
  * A batched launch takes its product path from its first handle.

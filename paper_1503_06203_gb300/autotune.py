@@ -1,7 +1,8 @@
 """Autotuner: the launch knobs that run a frame shape fastest on this GPU.
 
 Knobs (results never depend on them; see corr_set_option in include/xengine.h):
-the product path (tensor cores + dp4a, or tensor cores alone) and the time
+the product path (tensor cores + dp4a, tensor cores alone, or tensor cores +
+dp4a on offset-encoded operands with the Eq. 3 corrections) and the time
 split (automatic, or a fixed number of ranges). For a frame shape (N, F, T)
 the tuner times every candidate with CUDA events on random frames and keeps
 the fastest in a JSON cache keyed by the GPU and the shape, so a shape is
@@ -17,7 +18,7 @@ import os
 from . import CORR_OPT_PRODUCT, CORR_OPT_SPLIT, Correlator
 
 CACHE_ENV = "XE_TUNE_CACHE"
-PRODUCTS = (1, 0)      # tensor cores + dp4a, tensor cores alone
+PRODUCTS = (1, 0, 2)   # tensor cores + dp4a, tensor cores alone, offset-encoded operands (Eq. 3)
 SPLITS = (0, 1, 2, 4)  # automatic, fixed
 MARGIN = 0.01          # relative speed-up a candidate needs over the default
 

@@ -104,7 +104,13 @@ __device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
 // Lanes 16..31 load their rows in the order k ^ 1 and odd element quads
 // store their elements in the order slot ^ 1, so that loads and stores are
 // free of bank conflicts; runtime prmt selectors undo both reorderings.
-template <bool kMasked>
+//
+// kEnc (offset-encoded operands, the Eq. 3 route): the planes keep the
+// encoded nibbles, all unsigned: Xr = hi, Xi = lo, Xr + Xi = hi + lo (row
+// side) and Xr - Xi + 15 = (hi + 15) - lo (column side), each in [0, 30];
+// masked rows are 0x00, which zeroes every product they enter (each product
+// has a row-side factor Xr, Xi or Xr + Xi).
+template <bool kMasked, bool kEnc>
 __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, uint32_t pl1, uint32_t pl2,
                                             bool side_b, int eg, int tg, int p, int lo, int hi) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(box);
@@ -113,7 +119,7 @@ __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, ui
   for (int k = 0; k < 16; ++k) {
     const int t = 16 * tg + (k ^ p);
     r[k] = w[t * (kTile / 4) + eg];
-    if (kMasked) r[k] = (t >= lo && t < hi) ? r[k] : 0x88888888u;  // rows outside [lo, hi) read as 0 + 0i
+    if (kMasked) r[k] = (t >= lo && t < hi) ? r[k] : (kEnc ? 0u : 0x88888888u);  // rows outside [lo, hi): no products
   }
   const int s = eg & 1;
   const uint32_t selA = p ? 0x1504u : 0x5140u;  // interleave two rows, bytes 0-1
@@ -140,9 +146,15 @@ __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, ui
     for (int j = 0; j < 4; ++j) {
       const uint32_t hi = (wd[k][j] >> 4) & 0x0F0F0F0Fu;
       const uint32_t lo = wd[k][j] & 0x0F0F0F0Fu;
-      xr[j] = (hi + 0x78787878u) ^ 0x80808080u;
-      xi[j] = (lo + 0x78787878u) ^ 0x80808080u;
-      sd[j] = side_b ? (((hi | 0x80808080u) - lo) ^ 0x80808080u) : ((hi + lo + 0x70707070u) ^ 0x80808080u);
+      if (kEnc) {
+        xr[j] = hi;
+        xi[j] = lo;
+        sd[j] = side_b ? ((hi + 0x0F0F0F0Fu) - lo) : (hi + lo);
+      } else {
+        xr[j] = (hi + 0x78787878u) ^ 0x80808080u;
+        xi[j] = (lo + 0x78787878u) ^ 0x80808080u;
+        sd[j] = side_b ? (((hi | 0x80808080u) - lo) ^ 0x80808080u) : ((hi + lo + 0x70707070u) ^ 0x80808080u);
+      }
     }
     const uint32_t off = plane_off(e, tg);
     if (pl0) sts128(pl0 + off, xr[0], xr[1], xr[2], xr[3]);  // (0 = plane not wanted)
@@ -172,7 +184,7 @@ __device__ __forceinline__ void zero_acc(int32_t (&acc)[3][2][4]) {
 }
 
 // Tensor cores only, k-steps [0, ksteps) of the chunk.
-template <int sel>
+template <int sel, bool kEnc>
 __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
                                           int lane, int ksteps, int32_t (&acc)[3][2][4]) {
   const int arow = pr * 16 + (lane & 15);
@@ -190,7 +202,7 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
       ldsm_x4(pb + plane_off(brow, 2 * ks + bhalf), b[0][0], b[0][1], b[1][0], b[1][1]);
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
-        if (sub_on(sel, ni)) mma_s8_16832(acc[pl][ni], a[0], a[1], a[2], a[3], b[ni][0], b[ni][1]);
+        if (sub_on(sel, ni)) mma_8bit<kEnc>(acc[pl][ni], a[0], a[1], a[2], a[3], b[ni][0], b[ni][1]);
     }
   }
 }
@@ -205,7 +217,7 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // accumulator layout, so its dp4a work is those entries' dot products. The
 // dp4a work comes in blocks of 8 samples of one plane; the MMAs are spread
 // evenly over the blocks.
-template <int sel, int kMmaK>
+template <int sel, int kMmaK, bool kEnc>
 __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
                                              int lane, int32_t (&acc)[3][2][4]) {
   constexpr int kNi0 = sel == kSelN1 ? 1 : 0;  // first column sub-tile
@@ -229,7 +241,7 @@ __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base,
         ldsm_x4(pa + plane_off(arow, 2 * mks + ahalf), fa[0], fa[1], fa[2], fa[3]);
         ldsm_x4(pb + plane_off(brow, 2 * mks + bhalf), fb[0][0], fb[0][1], fb[1][0], fb[1][1]);
       }
-      if (sub_on(sel, mni)) mma_s8_16832(acc[mpl][mni], fa[0], fa[1], fa[2], fa[3], fb[mni][0], fb[mni][1]);
+      if (sub_on(sel, mni)) mma_8bit<kEnc>(acc[mpl][mni], fa[0], fa[1], fa[2], fa[3], fb[mni][0], fb[mni][1]);
     }
     // ---- integer ALU: samples 32*kMmaK + 8*grp .. +7 of plane dpl ----
     const int grp = k / 3, dpl = k % 3;
@@ -251,7 +263,7 @@ __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base,
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int c = 0; c < 2; ++c) dp4a_acc(acc[dpl][kNi0 + n][2 * h + c], av[h][wd], bv[n][c][wd]);
+          for (int c = 0; c < 2; ++c) dp4a_8bit<kEnc>(acc[dpl][kNi0 + n][2 * h + c], av[h][wd], bv[n][c][wd]);
   }
 }
 
@@ -371,7 +383,7 @@ struct Walk {
   }
 };
 
-template <bool kFrames>
+template <bool kFrames, bool kEnc>
 __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 CorrArgs args) {
   extern __shared__ uint8_t smem_raw[];
@@ -443,9 +455,9 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         const uint32_t pl2 = smem_u32(sm.plane[buf][j][kPsd]);
         if (diag && j == 1) pl0 = pl1 = 0;
         if (lo <= 0 && hi >= kTC)
-          unpack_unit<false>(box, pl0, pl1, pl2, j == 1, eg, tg, p, 0, kTC);
+          unpack_unit<false, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, 0, kTC);
         else
-          unpack_unit<true>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi);
+          unpack_unit<true, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi);
       }
       mbar_arrive(&sm.pfull[buf]);   // release this thread's plane stores
       mbar_arrive(&sm.bempty[s]);    // this thread is done reading box slot s
@@ -497,17 +509,17 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
       if (args.hybrid == 1 && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
         if (sel == kSelAll)
-          chunk_hybrid<kSelAll, 3>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelAll, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
         else if (sel == kSelN0)
-          chunk_hybrid<kSelN0, 3>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelN0, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
         else
-          chunk_hybrid<kSelN1, 3>(a_base, b01, b2, pr, pc, lane, acc);
+          chunk_hybrid<kSelN1, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
       } else if (sel == kSelAll) {
-        chunk_mma<kSelAll>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+        chunk_mma<kSelAll, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
       } else if (sel == kSelN0) {
-        chunk_mma<kSelN0>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+        chunk_mma<kSelN0, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
       } else {
-        chunk_mma<kSelN1>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+        chunk_mma<kSelN1, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
       }
     }
     __syncwarp();

@@ -76,6 +76,15 @@ __device__ __forceinline__ void mma_s8_16832(int32_t* d, uint32_t a0, uint32_t a
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Same shape with unsigned 8-bit operands (offset-encoded samples, 0..30).
+__device__ __forceinline__ void mma_u8_16832(int32_t* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                             uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.s32.u8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 // ---- byte permute -------------------------------------------------------------
 __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   uint32_t d;
@@ -120,6 +129,28 @@ namespace xe {
 // 4-way signed int8 dot product plus int32 add on the integer ALU pipe.
 __device__ __forceinline__ void dp4a_acc(int32_t& d, uint32_t a, uint32_t b) {
   asm volatile("dp4a.s32.s32 %0, %1, %2, %0;\n" : "+r"(d) : "r"(a), "r"(b));
+}
+
+__device__ __forceinline__ void dp4a_acc_u(int32_t& d, uint32_t a, uint32_t b) {
+  asm volatile("dp4a.u32.u32 %0, %1, %2, %0;\n" : "+r"(d) : "r"(a), "r"(b));
+}
+
+// Signed (kEnc = false) or unsigned (kEnc = true) 8-bit operands.
+template <bool kEnc>
+__device__ __forceinline__ void mma_8bit(int32_t* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+  if (kEnc)
+    mma_u8_16832(d, a0, a1, a2, a3, b0, b1);
+  else
+    mma_s8_16832(d, a0, a1, a2, a3, b0, b1);
+}
+
+template <bool kEnc>
+__device__ __forceinline__ void dp4a_8bit(int32_t& d, uint32_t a, uint32_t b) {
+  if (kEnc)
+    dp4a_acc_u(d, a, b);
+  else
+    dp4a_acc(d, a, b);
 }
 
 __device__ __forceinline__ void lds64(uint32_t addr, uint32_t& w0, uint32_t& w1) {

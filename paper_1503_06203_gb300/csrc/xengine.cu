@@ -14,6 +14,7 @@
 #include "xengine.h"
 #include "xe_corr.cuh"
 #include "xe_lags.cuh"
+#include "xe_offsets.cuh"
 
 namespace {
 
@@ -59,14 +60,17 @@ int device_setup(int dev) {
   std::lock_guard<std::mutex> lk(g_dev_mu);
   if (dev < 0 || dev >= 64) return fail(CORR_EINVAL, "device ordinal %d out of range", dev);
   if (g_dev_ready[dev]) return CORR_OK;
-  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kSmemBytes));
+  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel<false, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xe::corr_tile_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(xe::corr_tile_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kSmemBytes));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(xe::corr_tile_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel<false>, xe::kThreads, kSmemBytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel<false, false>, xe::kThreads, kSmemBytes);
   if (e != cudaSuccess || bps < 1)
     return fail(CORR_ECUDA, "occupancy query: %s (blocks/SM %d)", cudaGetErrorString(e), bps);
   int sms = 0;
@@ -87,13 +91,18 @@ int alloc_failed(const char* what, size_t bytes, cudaError_t e) {
   return fail(CORR_ENOMEM, "%s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
 }
 
-// Product path: 1 = tensor cores + dp4a (chunk_hybrid), 0 = tensor cores only.
-// XE_PRODUCT=mma in the environment selects the tensor-core-only path.
+// Product path: 1 = tensor cores + dp4a (chunk_hybrid), 0 = tensor cores only,
+// 2 = as 1 on offset-encoded operands with the Eq. 3 corrections (xe_offsets.cuh).
+// XE_PRODUCT=mma in the environment makes the tensor-core-only path the default.
 int product_hybrid() {
   const char* v = getenv("XE_PRODUCT");
   return (v && strcmp(v, "mma") == 0) ? 0 : 1;
 }
 const int g_hybrid = product_hybrid();
+
+int effective_product(int product) { return product < 0 ? g_hybrid : product; }
+// The kernel's chunk path: 1 = tensor cores + dp4a, 0 = tensor cores only.
+int chunk_hybrid_flag(int product) { return effective_product(product) == 0 ? 0 : 1; }
 
 // Upper-triangle tile order: block rows bi <= block columns bj, row-major (Fig. 1).
 void triangle_tiles(int32_t N, int32_t tile, std::vector<int32_t>& bi, std::vector<int32_t>& bj) {
@@ -143,6 +152,8 @@ struct corr_handle {
   int32_t hchunk_T = 0, tail_T = 0;
   cudaStream_t s_copy = nullptr, s_comp = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
+  // offset-encoded route: per-element nibble sums [F][N][2] of the current launch
+  int32_t* d_sums = nullptr;
 };
 
 namespace {
@@ -300,8 +311,32 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   CUtensorMap tm;
   int rc = make_tmap(&tm, frame, Np, h->F, pl.T);
   if (rc) return rc;
-  if (h->fresh && pl.split > 1)  // time-split items add atomically onto zeros
+  const bool enc = effective_product(h->product) == 2;
+  if (enc) {
+    // Eq. 3 route: nibble sums over this launch's samples, then the offset
+    // terms stored (fresh) or added into the accumulators; the correlator
+    // then adds the encoded products onto them
+    const size_t sbytes = static_cast<size_t>(h->F) * h->N * 2 * sizeof(int32_t);
+    if (!h->d_sums) {
+      cudaError_t e = cudaMalloc(&h->d_sums, sbytes);
+      if (e != cudaSuccess) {
+        h->d_sums = nullptr;
+        return alloc_failed("nibble sums", sbytes, e);
+      }
+    }
+    XE_CHECK(h, cudaMemsetAsync(h->d_sums, 0, sbytes, st));
+    const int64_t words = static_cast<int64_t>(h->F) * (Np / 4);
+    const dim3 sg(static_cast<unsigned>(ceil_div(words, xe::kSumThreads)), static_cast<unsigned>(ceil_div(pl.T, xe::kSumRows)));
+    xe::nibble_sums_kernel<<<sg, xe::kSumThreads, 0, st>>>(frame, h->N, Np, h->F, pl.T, h->d_sums);
+    XE_CHECK(h, cudaGetLastError());
+    xe::offset_seed_kernel<<<static_cast<unsigned>(static_cast<int64_t>(h->F) * h->N), 256, 0, st>>>(
+        h->d_sums, h->N, h->B, pl.T, h->fresh ? 0 : 1, h->acc);
+    XE_CHECK(h, cudaGetLastError());
+    h->launches += 2;
+    h->fresh = false;  // the correlator adds onto the seeded terms
+  } else if (h->fresh && pl.split > 1) {  // time-split items add atomically onto zeros
     XE_CHECK(h, cudaMemsetAsync(h->acc, 0, static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t), st));
+  }
   xe::CorrArgs a;
   a.items = pl.d_items;
   a.nitems = pl.nitems;
@@ -311,9 +346,12 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.B = h->B;
   a.vis = h->acc;
   a.fresh = h->fresh ? 1 : 0;
-  a.hybrid = h->product < 0 ? g_hybrid : h->product;
+  a.hybrid = chunk_hybrid_flag(h->product);
   a.err = h->d_err;
-  xe::corr_tile_kernel<false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  if (enc)
+    xe::corr_tile_kernel<false, true><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  else
+    xe::corr_tile_kernel<false, false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
   ++h->launches;
   h->fresh = false;
@@ -514,7 +552,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel<true>);
+  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel<true, false>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -617,7 +655,7 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
     d.t0 = 0;
     d.atomic = 0;
   }
-  const int hybrid = hs[0]->product < 0 ? g_hybrid : hs[0]->product;
+  const int hybrid = chunk_hybrid_flag(hs[0]->product);
   if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_err != hs[0]->d_err)
     if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err, hybrid))) return rc;
@@ -770,7 +808,7 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     d.t0 = empty ? 1 : segs[s].t0;  // t0 > T: nothing is valid
     d.atomic = 1;
   }
-  const int hybrid = h0->product < 0 ? g_hybrid : h0->product;
+  const int hybrid = chunk_hybrid_flag(h0->product);
   if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_err != h0->d_err)
     if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid))) return rc;
@@ -1013,7 +1051,7 @@ int corr_set_option(corr_handle_t* h, int option, int64_t value) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (option == CORR_OPT_PRODUCT) {
-    if (value < -1 || value > 1) return fail(CORR_EINVAL, "CORR_OPT_PRODUCT must be -1, 0 or 1");
+    if (value < -1 || value > 2) return fail(CORR_EINVAL, "CORR_OPT_PRODUCT must be -1, 0, 1 or 2");
     h->product = static_cast<int>(value);
     return CORR_OK;
   }
@@ -1043,7 +1081,7 @@ int corr_set_option(corr_handle_t* h, int option, int64_t value) {
 
 int64_t corr_get_option(const corr_handle_t* h, int option) {
   if (!h) return fail(CORR_EINVAL, "NULL handle");
-  if (option == CORR_OPT_PRODUCT) return h->product < 0 ? g_hybrid : h->product;
+  if (option == CORR_OPT_PRODUCT) return effective_product(h->product);
   if (option == CORR_OPT_SPLIT) return h->split_opt;
   return fail(CORR_EINVAL, "unknown option %d", option);
 }
@@ -1104,6 +1142,7 @@ void corr_destroy(corr_handle_t* h) {
   free_plan(&h->plan_chunk);
   free_plan(&h->plan_tail);
   if (h->stage) cudaFree(h->stage);
+  if (h->d_sums) cudaFree(h->d_sums);
   for (int k = 0; k < 2; ++k) {
     if (h->hchunk[k]) cudaFree(h->hchunk[k]);
     if (h->ev_copied[k]) cudaEventDestroy(h->ev_copied[k]);
@@ -1263,7 +1302,7 @@ extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int3
   a.hybrid = 0;
   a.err = reinterpret_cast<int32_t*>(scratch);
   const int grid = static_cast<int>(std::min<int64_t>(slots, nitems));
-  xe::corr_tile_kernel<false><<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  xe::corr_tile_kernel<false, false><<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(CORR_ECUDA, "noalloc correlate: %s", cudaGetErrorString(e));
   if (status_dev && (e = cudaMemcpyAsync(status_dev, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) !=
                         cudaSuccess)
