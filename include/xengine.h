@@ -95,8 +95,12 @@ int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream);
  * corr_accumulate_host -- as corr_accumulate with packed_host in host memory
  * (pinned memory gives full copy speed; pageable memory works). The frame
  * is copied to the device in time-chunks, each chunk correlated while the
- * next one is copied. The host buffer must stay unchanged until the stream
- * has passed this call.
+ * next one is copied. The copies wait only for the handle's chunk buffers,
+ * not for work already queued on `stream`: they may overlap the previous
+ * frame's correlation and readout. So the frame must be in host memory when
+ * the call is made (not produced later by work queued on `stream`), and it
+ * must stay unchanged until the stream has passed this call. The
+ * correlation itself runs after everything queued on `stream` before.
  */
 int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* stream);
 

@@ -888,17 +888,20 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
     h->tail_T = h->T % h->hchunk_T;
     if (h->tail_T && (rc = build_plan(h, h->tail_T, &h->plan_tail))) return rc;
   }
-  // internal streams start after everything already queued on `st` (and the handle's last call)
+  // the correlation starts after everything already queued on `st` (and the
+  // handle's last call); the copies wait only for their chunk buffer to be
+  // free, so they overlap the previous frame's correlation and readout
   if ((rc = order_after_last(h, st))) return rc;
   XE_CHECK(h, cudaEventRecord(h->ev_in, st));
-  XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_in, 0));
   XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_in, 0));
   const int32_t nchunks = static_cast<int32_t>(ceil_div(h->T, h->hchunk_T));
   for (int32_t c = 0; c < nchunks; ++c) {
     const int b = c & 1;
     const int32_t t0 = c * h->hchunk_T;
     const int32_t cT = std::min(h->hchunk_T, h->T - t0);
-    if (c >= 2) XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_used[b], 0));
+    // buffer b's last reader: chunk c - 2 of this call, or the last chunk on b
+    // of an earlier call (an event never recorded is passed at once)
+    XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_used[b], 0));
     if (Np == h->N) {
       XE_CHECK(h, cudaMemcpyAsync(h->hchunk[b], packed_host + static_cast<size_t>(t0) * row,
                                   static_cast<size_t>(cT) * row, cudaMemcpyHostToDevice, h->s_copy));
