@@ -865,9 +865,11 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
   const int32_t Np = static_cast<int32_t>(ceil_div(h->N, 16) * 16);
   const size_t row = static_cast<size_t>(h->F) * h->N;  // bytes per time sample (host layout)
   if (!h->s_copy) {
-    // chunk of about T/4 samples (a stage multiple), at most 256 MB per buffer
-    int64_t cT = ceil_div(ceil_div(h->T, 4), xe::kTC) * xe::kTC;
-    const int64_t cap = std::max<int64_t>(xe::kTC, ((int64_t(256) << 20) / (int64_t(h->F) * Np)) / xe::kTC * xe::kTC);
+    // chunk of about T/2 samples (a stage multiple), at most 1 GiB per buffer:
+    // with copies overlapping the previous frame, the correlation is the
+    // longer chain, and larger chunks run it more efficiently
+    int64_t cT = ceil_div(ceil_div(h->T, 2), xe::kTC) * xe::kTC;
+    const int64_t cap = std::max<int64_t>(xe::kTC, ((int64_t(1) << 30) / (int64_t(h->F) * Np)) / xe::kTC * xe::kTC);
     cT = std::max<int64_t>(xe::kTC, std::min<int64_t>(cT, cap));
     cT = std::min<int64_t>(cT, ceil_div(h->T, xe::kTC) * xe::kTC);
     h->hchunk_T = static_cast<int32_t>(cT);
