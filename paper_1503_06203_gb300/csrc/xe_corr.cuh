@@ -331,7 +331,7 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // Walks (item, chunk) pairs of this CTA in order. T and nch are the current
 // item's frame's (from its descriptor in a batch, else from args); the writer
 // reads the rest when it needs it.
-template <bool kFrames>
+template <bool kFrames, bool kHold>
 struct Walk {
   int item, c, f, bi, bj, c1, frame, T, nch, T0;
   const int4* items;
@@ -344,7 +344,7 @@ struct Walk {
       c = w.z;
       c1 = w.w;
       if (kFrames) {
-        bj = (w.y >> 16) & 0x7FFF;  // (bit 31: hold, read by the writer)
+        bj = kHold ? (w.y >> 16) & 0x7FFF : w.y >> 16;  // (bit 31: hold, read by the writer)
         f = w.x & 0xFFFFF;
         const int fr = w.x >> 20;
         if (fr != frame) {
@@ -383,9 +383,15 @@ struct Walk {
   }
 };
 
-template <bool kFrames, bool kEnc>
+// kMode: kSingle = one frame (args), kBatch = per-frame descriptors, kGated =
+// descriptors plus hold bits (a gated (tile, gate) group's segments).
+enum : int { kSingle = 0, kBatch = 1, kGated = 2 };
+
+template <int kMode, bool kEnc>
 __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 CorrArgs args) {
+  constexpr bool kFrames = kMode != kSingle;
+  constexpr bool kHold = kMode == kGated;
   extern __shared__ uint8_t smem_raw[];
   CorrSmem& sm = *reinterpret_cast<CorrSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                               ~static_cast<uintptr_t>(127));
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const int uw = warp - kMmaWarps;  // 0..3
     const bool producer = uw == 0 && lane == 0;
     const int eg = lane & 15, p = lane >> 4, tg = 2 * uw + p;  // samples 16tg..16tg+15 of each chunk
-    Walk<kFrames> ld;  // the TMA issuer walks the same units, kStages ahead
+    Walk<kFrames, kHold> ld;  // the TMA issuer walks the same units, kStages ahead
     ld.start(args);
     uint32_t issued = 0;
     const CUtensorMap* fenced = nullptr;
@@ -433,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     }
     uint32_t it = 0;
     bool ok = true;
-    Walk<kFrames> x;
+    Walk<kFrames, kHold> x;
     for (x.start(args); x.valid(); x.next(), ++it) {
       const bool diag = x.bi == x.bj;
       const int s = it % kStages, buf = it % kPlaneBufs;
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   int32_t acc[3][2][4];
   zero_acc(acc);
   uint32_t it = 0;
-  Walk<kFrames> x;
+  Walk<kFrames, kHold> x;
   for (x.start(args); x.valid(); ++it) {
     const bool diag = x.bi == x.bj;
     const int buf = it % kPlaneBufs;
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
     if (x.c + 1 == x.c1) {  // end of the item: write it, unless it holds its sums for the CTA's next item
       const int4 w = args.items[x.item];
-      if (!kFrames || w.y >= 0) {
+      if (!kHold || w.y >= 0) {
       const bool whole = w.z == 0 && w.w == x.nch;
       const FrameDesc* d = kFrames ? &args.frames[x.frame] : nullptr;
       const int fresh = d ? d->fresh : args.fresh;

@@ -60,17 +60,17 @@ int device_setup(int dev) {
   std::lock_guard<std::mutex> lk(g_dev_mu);
   if (dev < 0 || dev >= 64) return fail(CORR_EINVAL, "device ordinal %d out of range", dev);
   if (g_dev_ready[dev]) return CORR_OK;
-  cudaError_t e = cudaFuncSetAttribute(xe::corr_tile_kernel<false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xe::corr_tile_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(xe::corr_tile_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kSmemBytes));
+  cudaError_t e = cudaSuccess;
+  for (const void* k : {reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGated, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, true>)})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
   int bps = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel<false, false>, xe::kThreads, kSmemBytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::corr_tile_kernel<xe::kSingle, false>, xe::kThreads,
+                                                    kSmemBytes);
   if (e != cudaSuccess || bps < 1)
     return fail(CORR_ECUDA, "occupancy query: %s (blocks/SM %d)", cudaGetErrorString(e), bps);
   int sms = 0;
@@ -349,9 +349,9 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.hybrid = chunk_hybrid_flag(h->product);
   a.err = h->d_err;
   if (enc)
-    xe::corr_tile_kernel<false, true><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+    xe::corr_tile_kernel<xe::kSingle, true><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   else
-    xe::corr_tile_kernel<false, false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+    xe::corr_tile_kernel<xe::kSingle, false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
   ++h->launches;
   h->fresh = false;
@@ -473,7 +473,7 @@ struct BatchSet {
   cudaEvent_t done = nullptr;  // after the last graph launch that read this set
   bool pending = false;
   cudaGraphExec_t exec = nullptr;
-  int64_t key_frames = -1, key_items = -1, key_grid = -1, key_hybrid = -1;
+  int64_t key_frames = -1, key_items = -1, key_grid = -1, key_hybrid = -1, key_gated = -1;
   int32_t* key_err = nullptr;
 };
 
@@ -521,7 +521,7 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
   return CORR_OK;
 }
 
-int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid) {
+int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid, bool gated) {
   if (b.exec) {
     cudaGraphExecDestroy(b.exec);
     b.exec = nullptr;
@@ -552,7 +552,8 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = reinterpret_cast<void*>(xe::corr_tile_kernel<true, false>);
+  kp.func = gated ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>)
+                  : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -568,6 +569,7 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   b.key_items = nitems;
   b.key_grid = grid;
   b.key_hybrid = hybrid;
+  b.key_gated = gated ? 1 : 0;
   b.key_err = err;
   return CORR_OK;
 }
@@ -657,8 +659,8 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
   }
   const int hybrid = chunk_hybrid_flag(hs[0]->product);
   if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
-      b.key_err != hs[0]->d_err)
-    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err, hybrid))) return rc;
+      b.key_gated != 0 || b.key_err != hs[0]->d_err)
+    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err, hybrid, false))) return rc;
   cudaError_t e = cudaGraphLaunch(b.exec, st);
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
   if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
@@ -810,8 +812,8 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
   }
   const int hybrid = chunk_hybrid_flag(h0->product);
   if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
-      b.key_err != h0->d_err)
-    if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid))) return rc;
+      b.key_gated != 1 || b.key_err != h0->d_err)
+    if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid, true))) return rc;
   cudaError_t e = cudaGraphLaunch(b.exec, st);
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
   if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
@@ -1307,7 +1309,7 @@ extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int3
   a.hybrid = 0;
   a.err = reinterpret_cast<int32_t*>(scratch);
   const int grid = static_cast<int>(std::min<int64_t>(slots, nitems));
-  xe::corr_tile_kernel<false, false><<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  xe::corr_tile_kernel<xe::kSingle, false><<<grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(CORR_ECUDA, "noalloc correlate: %s", cudaGetErrorString(e));
   if (status_dev && (e = cudaMemcpyAsync(status_dev, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st)) !=
                         cudaSuccess)
