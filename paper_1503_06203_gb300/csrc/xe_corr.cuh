@@ -73,13 +73,30 @@ struct CorrArgs {
   int32_t* err;         // device error word
 };
 
+// What a chunk's consumers need to know (batched and gated launches): the
+// TMA issuer writes it beside the chunk's box, the unpack warps pass it on
+// beside the planes, so no consumer loads work items or frame descriptors
+// from global memory on its critical path.
+struct ChunkMeta {
+  int32_t f;        // band
+  int32_t bij;      // bi | bj << 16
+  int32_t lo, hi;   // valid rows of the chunk: [lo, hi)
+  int32_t flags;    // kMetaValid | kMetaEnd | write mode << 4 (kMetaEnd unset while a gated group holds)
+  int32_t N;
+  int64_t B;
+  int32_t* vis;
+};
+enum : int { kMetaValid = 1, kMetaEnd = 2 };
+
 struct __align__(128) CorrSmem {
   uint8_t box[kStages][2][kBoxBytes];          // TMA ring: [stage][A|B][time][element]
   uint8_t plane[kPlaneBufs][2][3][kPlaneBytes];  // [buffer][A|B][slot][element][time]
   uint64_t full[kStages];   // box landed (TMA transaction count)
   uint64_t bempty[kStages]; // box read by all 128 unpack threads
   uint64_t pfull[kPlaneBufs];   // plane buffer written (128 unpack threads)
-  uint64_t pempty[kPlaneBufs];  // plane buffer read (4 product warps)
+  uint64_t pempty[kPlaneBufs];  // plane buffer read (16 product warps)
+  ChunkMeta meta[kStages];      // per box slot (batched and gated launches)
+  ChunkMeta pmeta[kPlaneBufs];  // per plane buffer (batched and gated launches)
 };
 
 // Swizzle of a plane (rows of kTC = 128 bytes, 8 chunks of 16): chunk c of
@@ -337,6 +354,11 @@ struct Walk {
   const int4* items;
   const FrameDesc* frames;
   int nitems, stride;
+  // batched and gated launches (the TMA issuer's walk): the current item's
+  // write mode and hold bit, the current frame's output
+  int mode, hold, fN, fresh, atomic;
+  int64_t fB;
+  int32_t* fvis;
   __device__ __forceinline__ void load() {
     if (item < nitems) {
       const int4 w = items[item];
@@ -352,7 +374,16 @@ struct Walk {
           T = frames[fr].T;
           nch = frames[fr].nch;
           T0 = frames[fr].t0;
+          fN = frames[fr].N;
+          fB = frames[fr].B;
+          fvis = frames[fr].vis;
+          fresh = frames[fr].fresh;
+          atomic = frames[fr].atomic;
         }
+        hold = kHold && w.y < 0;
+        // a gated group covers all of its gate's samples in the frame, like a whole tile
+        const bool whole = kHold || (w.z == 0 && w.w == nch);
+        mode = atomic ? 2 : (whole ? (fresh ? 0 : 1) : 2);
       } else {
         bj = w.y >> 16;
         f = w.x;
@@ -382,6 +413,44 @@ struct Walk {
     return kFrames ? &frames[frame].map : single;
   }
 };
+
+// Off-diagonal tile: warp w takes piece (w / 4, w % 4); warps w, w+4, w+8,
+// w+12 share SM sub-partition w % 4.
+// Diagonal tile: the 10 pieces on or above the diagonal hold its 20 needed
+// 16 x 8 sub-tiles. Eight pieces go whole to warps 0-7; pieces (2,2) and
+// (3,3) are split into single sub-tiles for warps 8-11; warps 12-15 idle.
+// Each sub-partition then runs 5 sub-tiles (8 on a full tile).
+// (2 bits per warp: piece row, piece column, selection)
+constexpr uint32_t kDiagR = 0xfa9050u, kDiagC = 0xfaedd8u, kDiagSel = 0xff990000u;
+
+// One product warp's share of one chunk in plane buffer `buf`; nvalid = valid
+// rows of the chunk. Returns the warp's piece (pr, pc) and selection.
+template <bool kEnc>
+__device__ __forceinline__ void product_chunk(CorrSmem& sm, int buf, int warp, int lane, bool diag, int nvalid,
+                                              int hybrid, int& pr, int& pc, int& sel, int32_t (&acc)[3][2][4]) {
+  pr = diag ? static_cast<int>((kDiagR >> (2 * warp)) & 3) : warp >> 2;
+  pc = diag ? static_cast<int>((kDiagC >> (2 * warp)) & 3) : warp & 3;
+  sel = diag ? static_cast<int>((kDiagSel >> (2 * warp)) & 3) : kSelAll;
+  if (sel == kSelIdle) return;
+  const uint32_t a_base = smem_u32(sm.plane[buf][0][0]);
+  const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
+  const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
+  const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
+  if (hybrid == 1 && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
+    if (sel == kSelAll)
+      chunk_hybrid<kSelAll, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+    else if (sel == kSelN0)
+      chunk_hybrid<kSelN0, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+    else
+      chunk_hybrid<kSelN1, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+  } else if (sel == kSelAll) {
+    chunk_mma<kSelAll, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+  } else if (sel == kSelN0) {
+    chunk_mma<kSelN0, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+  } else {
+    chunk_mma<kSelN1, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
+  }
+}
 
 // kMode: kSingle = one frame (args), kBatch = per-frame descriptors, kGated =
 // descriptors plus hold bits (a gated (tile, gate) group's segments).
@@ -427,18 +496,91 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         tensormap_acquire(map);
         fenced = map;
       }
+      if constexpr (kFrames) {  // the chunk's consumers read this instead of the work list
+        ChunkMeta& m = sm.meta[s];
+        m.f = ld.f;
+        m.bij = ld.bi | (ld.bj << 16);
+        m.lo = ld.T0 - ld.c * kTC;
+        m.hi = ld.T - ld.c * kTC;
+        m.flags = kMetaValid | ((ld.c + 1 == ld.c1 && !ld.hold) ? kMetaEnd : 0) | (ld.mode << 4);
+        m.N = ld.fN;
+        m.B = ld.fB;
+        m.vis = ld.fvis;
+      }
+      // (the arrive releases the stores above to the slot's waiters)
       mbar_arrive_expect_tx(&sm.full[s], diag ? kBoxBytes : 2 * kBoxBytes);
       tma_load_3d(sm.box[s][0], map, &sm.full[s], ld.bi * kTile, ld.f, ld.c * kTC);
       if (!diag) tma_load_3d(sm.box[s][1], map, &sm.full[s], ld.bj * kTile, ld.f, ld.c * kTC);
       ++issued;
       ld.next();
     };
+    // batched and gated launches end the chunk stream with an entry without
+    // kMetaValid (no copy; a plain arrive completes its phase)
+    bool ended = false;
+    auto issue_end = [&](void) {
+      const int s = issued % kStages;
+      sm.meta[s].flags = 0;
+      mbar_arrive(&sm.full[s]);
+      ++issued;
+      ended = true;
+    };
     if (producer) {
       if (!kFrames) tma_prefetch_desc(&tmap);
-      for (int k = 0; k < kStages && ld.valid(); ++k) issue();
+      for (int k = 0; k < kStages; ++k) {
+        if (ld.valid()) {
+          issue();
+        } else {
+          if (kFrames) issue_end();
+          break;
+        }
+      }
     }
     uint32_t it = 0;
     bool ok = true;
+    if constexpr (kFrames) {
+      for (;; ++it) {
+        const int s = it % kStages, buf = it % kPlaneBufs;
+        if ((it >= kPlaneBufs && !mbar_wait_bounded(&sm.pempty[buf], ((it / kPlaneBufs) - 1) & 1, kSpinLimit)) ||
+            !mbar_wait_bounded(&sm.full[s], (it / kStages) & 1, kSpinLimit)) {
+          if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
+          ok = false;
+          break;
+        }
+        const ChunkMeta& m = sm.meta[s];
+        const int flags = m.flags, bij = m.bij, lo = m.lo, hi = m.hi;
+        if (threadIdx.x == kMmaWarps * 32) sm.pmeta[buf] = m;  // passed on with the planes
+        if (!(flags & kMetaValid)) {
+          mbar_arrive(&sm.pfull[buf]);
+          break;
+        }
+        const bool diag = (bij & 0xFFFF) == (bij >> 16);
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+          const uint8_t* box = sm.box[s][diag ? 0 : j];
+          uint32_t pl0 = smem_u32(sm.plane[buf][j][kPxr]);
+          uint32_t pl1 = smem_u32(sm.plane[buf][j][kPxi]);
+          const uint32_t pl2 = smem_u32(sm.plane[buf][j][kPsd]);
+          if (diag && j == 1) pl0 = pl1 = 0;
+          if (lo <= 0 && hi >= kTC)
+            unpack_unit<false, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, 0, kTC);
+          else
+            unpack_unit<true, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi);
+        }
+        mbar_arrive(&sm.pfull[buf]);
+        mbar_arrive(&sm.bempty[s]);
+        if (producer && !ended) {  // refill slot s once every unpack thread is done with it
+          if (!mbar_wait_bounded(&sm.bempty[s], (it / kStages) & 1, kSpinLimit)) {
+            atomicOr(args.err, kErrTimeoutEmpty);
+            ok = false;
+            break;
+          }
+          if (ld.valid())
+            issue();
+          else
+            issue_end();
+        }
+      }
+    } else {
     Walk<kFrames, kHold> x;
     for (x.start(args); x.valid(); x.next(), ++it) {
       const bool diag = x.bi == x.bj;
@@ -476,6 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         issue();
       }
     }
+    }
     if (producer) {  // never leave with copies in flight (bounded)
       const uint32_t first = issued > kStages ? issued - kStages : 0;
       for (uint32_t k = first; k < issued; ++k)
@@ -485,17 +628,34 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   }
 
   // ================= product warps =================
-  // Off-diagonal tile: warp w takes piece (w / 4, w % 4); warps w, w+4, w+8,
-  // w+12 share SM sub-partition w % 4.
-  // Diagonal tile: the 10 pieces on or above the diagonal hold its 20 needed
-  // 16 x 8 sub-tiles. Eight pieces go whole to warps 0-7; pieces (2,2) and
-  // (3,3) are split into single sub-tiles for warps 8-11; warps 12-15 idle.
-  // Each sub-partition then runs 5 sub-tiles (8 on a full tile).
-  // (2 bits per warp: piece row, piece column, selection)
-  constexpr uint32_t kDiagR = 0xfa9050u, kDiagC = 0xfaedd8u, kDiagSel = 0xff990000u;
   int32_t acc[3][2][4];
   zero_acc(acc);
   uint32_t it = 0;
+  if constexpr (kFrames) {
+    for (;; ++it) {
+      const int buf = it % kPlaneBufs;
+      if (!mbar_wait_bounded(&sm.pfull[buf], (it / kPlaneBufs) & 1, kSpinLimit)) {
+        if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
+        return;
+      }
+      const ChunkMeta& m = sm.pmeta[buf];
+      const int flags = m.flags;
+      if (!(flags & kMetaValid)) return;  // end of this CTA's chunks
+      const int bi = m.bij & 0xFFFF, bj = m.bij >> 16;
+      int pr, pc, sel;
+      product_chunk<kEnc>(sm, buf, warp, lane, bi == bj, m.hi, args.hybrid, pr, pc, sel, acc);
+      // the writer's fields, read before the buffer (and its metadata) is released
+      const int f = m.f, N = m.N;
+      const int64_t B = m.B;
+      int32_t* const vis = m.vis;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.pempty[buf]);
+      if (flags & kMetaEnd) {  // end of the item (a gated group's last segment): write it
+        if (sel != kSelIdle) write_piece(N, B, vis, f, bi * kTile, bj * kTile, pr, pc, lane, (flags >> 4) & 3, sel, acc);
+        zero_acc(acc);
+      }
+    }
+  } else {
   Walk<kFrames, kHold> x;
   for (x.start(args); x.valid(); ++it) {
     const bool diag = x.bi == x.bj;
@@ -504,46 +664,20 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       if (lane == 0) atomicOr(args.err, kErrTimeoutFull);
       return;
     }
-    const int pr = diag ? static_cast<int>((kDiagR >> (2 * warp)) & 3) : warp >> 2;
-    const int pc = diag ? static_cast<int>((kDiagC >> (2 * warp)) & 3) : warp & 3;
-    const int sel = diag ? static_cast<int>((kDiagSel >> (2 * warp)) & 3) : kSelAll;
-    if (sel != kSelIdle) {
-      const int nvalid = x.T - x.c * kTC;
-      const uint32_t a_base = smem_u32(sm.plane[buf][0][0]);
-      const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
-      const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
-      const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
-      if (args.hybrid == 1 && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
-        if (sel == kSelAll)
-          chunk_hybrid<kSelAll, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
-        else if (sel == kSelN0)
-          chunk_hybrid<kSelN0, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
-        else
-          chunk_hybrid<kSelN1, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
-      } else if (sel == kSelAll) {
-        chunk_mma<kSelAll, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
-      } else if (sel == kSelN0) {
-        chunk_mma<kSelN0, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
-      } else {
-        chunk_mma<kSelN1, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
-      }
-    }
+    int pr, pc, sel;
+    product_chunk<kEnc>(sm, buf, warp, lane, diag, x.T - x.c * kTC, args.hybrid, pr, pc, sel, acc);
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
-    if (x.c + 1 == x.c1) {  // end of the item: write it, unless it holds its sums for the CTA's next item
+    if (x.c + 1 == x.c1) {  // end of the item: write it
       const int4 w = args.items[x.item];
-      if (!kHold || w.y >= 0) {
       const bool whole = w.z == 0 && w.w == x.nch;
-      const FrameDesc* d = kFrames ? &args.frames[x.frame] : nullptr;
-      const int fresh = d ? d->fresh : args.fresh;
-      const int mode = (d && d->atomic) ? 2 : (whole ? (fresh ? 0 : 1) : 2);
+      const int mode = whole ? (args.fresh ? 0 : 1) : 2;
       if (sel != kSelIdle)
-        write_piece(d ? d->N : args.N, d ? d->B : args.B, d ? d->vis : args.vis, x.f, x.bi * kTile, x.bj * kTile, pr,
-                    pc, lane, mode, sel, acc);
+        write_piece(args.N, args.B, args.vis, x.f, x.bi * kTile, x.bj * kTile, pr, pc, lane, mode, sel, acc);
       zero_acc(acc);
-      }
     }
     x.next();
+  }
   }
 }
 

@@ -725,12 +725,14 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
   if ((rc = stage_if_needed(h0, in, T, st, &frame, &np))) return rc;
   CUtensorMap map;
   if ((rc = make_tmap(&map, frame, np, h0->F, T))) return rc;
-  // segments add atomically: fresh gates start from zero
-  for (int g = 0; g < G; ++g)
-    if (gates[g]->fresh) {
-      XE_CHECK(gates[g], cudaMemsetAsync(gates[g]->acc, 0, static_cast<size_t>(h0->F) * h0->B * 2 * sizeof(int32_t), st));
-      gates[g]->fresh = false;
-    }
+  // Each (band, tile, gate) group is written once, by one CTA, with every
+  // sample of its gate in this frame: stored into a fresh gate, added into
+  // one that holds sums; no atomics. A gate with no samples here stays as it is.
+  std::vector<int32_t> gate_fresh(G);
+  for (int g = 0; g < G; ++g) {
+    gate_fresh[g] = gates[g]->fresh ? 1 : 0;
+    if (per_gate[g] > 0) gates[g]->fresh = false;
+  }
   // groups: one (band, tile, gate) with all its segments in time order, run by
   // one CTA back to back ("hold" between them) and written once; groups are
   // dealt to CTAs longest-first onto the least-loaded CTA
@@ -778,10 +780,10 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
   size_t rows = 0;
   for (const auto& col : column) rows = std::max(rows, col.size());
   // CTA c's r-th item sits at r*grid + c. Shorter columns are padded with one-chunk
-  // items over an extra, empty segment (every sample masked), which add zeros.
+  // items over an extra, empty segment (every sample masked) that hold (never write).
   const int64_t nitems = static_cast<int64_t>(rows) * grid;
   const int64_t nseg = static_cast<int64_t>(segs.size()) + 1;
-  const int4 pad = make_int4(static_cast<int32_t>(segs.size()) << 20, 0, 0, 1);
+  const int4 pad = make_int4(static_cast<int32_t>(segs.size()) << 20, static_cast<int32_t>(0x80000000u), 0, 1);
   if (nitems > INT32_MAX || h0->F >= (1 << 20)) return fail(CORR_EINVAL, "gated: work list too large");
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -804,11 +806,11 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     d.N = h0->N;
     d.T = empty ? 0 : segs[s].t1;
     d.nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
-    d.fresh = 0;
+    d.fresh = empty ? 0 : gate_fresh[segs[s].g];
     d.B = h0->B;
     d.vis = gates[empty ? 0 : segs[s].g]->acc;
     d.t0 = empty ? 1 : segs[s].t0;  // t0 > T: nothing is valid
-    d.atomic = 1;
+    d.atomic = 0;
   }
   const int hybrid = chunk_hybrid_flag(h0->product);
   if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
