@@ -734,8 +734,11 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     if (per_gate[g] > 0) gates[g]->fresh = false;
   }
   // groups: one (band, tile, gate) with all its segments in time order, run by
-  // one CTA back to back ("hold" between them) and written once; groups are
-  // dealt to CTAs longest-first onto the least-loaded CTA
+  // one CTA back to back ("hold" between them) and written once. Groups are
+  // dealt in (band, gate, tile) order, each onto the least-loaded CTA: CTAs
+  // running at the same time then hold the tiles of one band and gate, walk
+  // the same chunks and share their input in L2 (with many groups per CTA the
+  // greedy deal stays within one group of balance)
   std::vector<int32_t> bi, bj;
   triangle_tiles(h0->N, xe::kTile, bi, bj);
   std::vector<std::vector<int32_t>> gate_segs(G);
@@ -746,14 +749,13 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
   };
   std::vector<Group> groups;
   for (int32_t f = 0; f < h0->F; ++f)
-    for (size_t u = 0; u < bi.size(); ++u)
-      for (int g = 0; g < G; ++g) {
-        if (gate_segs[g].empty()) continue;
-        double c = 0.0;
-        for (int32_t s : gate_segs[g]) c += ceil_div(segs[s].t1, xe::kTC) - segs[s].t0 / xe::kTC;
+    for (int g = 0; g < G; ++g) {
+      if (gate_segs[g].empty()) continue;
+      double c = 0.0;
+      for (int32_t s : gate_segs[g]) c += ceil_div(segs[s].t1, xe::kTC) - segs[s].t0 / xe::kTC;
+      for (size_t u = 0; u < bi.size(); ++u)
         groups.push_back({f, static_cast<int32_t>(u), g, c * (bi[u] == bj[u] ? kDiagCost : 1.0)});
-      }
-  std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.cost > b.cost; });
+    }
   const int dev = h0->device;
   const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
   const int64_t grid = std::min<int64_t>(slots, static_cast<int64_t>(groups.size()));
