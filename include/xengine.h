@@ -264,6 +264,17 @@ double corr_effective_ops(int32_t N, int32_t F, int32_t T);
 int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int32_t F, int32_t T, int32_t* vis_dev,
                            int32_t* status_dev, void* stream);
 
+/*
+ * corr_selftest_wait_timeout -- exercise the bounded device wait every kernel
+ * of this library uses (no counterpart in the paper). One CTA waits on a
+ * shared-memory barrier that nothing arrives on, polling at most `polls`
+ * times (1 .. 2^20), then records that the wait ran out and returns; the
+ * context stays usable. Synchronous on `stream`. Returns CORR_ETIMEOUT when
+ * the wait ran out (the expected outcome), CORR_OK if it did not, CORR_EINVAL
+ * for polls outside the range, CORR_ECUDA on a CUDA failure.
+ */
+int corr_selftest_wait_timeout(int32_t polls, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,7 +14,7 @@ from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_
                    CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "plan_schedule", "correlate_noalloc", "shift_lags", "accumulate_gated", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "correlate_noalloc", "selftest_wait_timeout", "shift_lags", "accumulate_gated", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -213,6 +213,12 @@ def correlate_noalloc(x, out, status=None, stream=None):
                                        ctypes.c_void_p(status.data_ptr()) if status is not None else None,
                                        _stream_ptr(stream)))
     return out
+
+
+def selftest_wait_timeout(polls: int = 4096, stream=None) -> int:
+    """Run the library's bounded device wait on a barrier nothing arrives on; returns the status code
+    (CORR_ETIMEOUT expected). The context stays usable afterwards."""
+    return int(lib().corr_selftest_wait_timeout(int(polls), _stream_ptr(stream)))
 
 
 def accumulate_batch(correlators, inputs, stream=None):

@@ -46,6 +46,7 @@ SIGNATURES = [
     ("corr_plan_schedule", _i64, [_i32, _i32, _i32, _i32, _vp, _i64, _vp]),
     ("corr_effective_ops", ctypes.c_double, [_i32, _i32, _i32]),
     ("corr_correlate_noalloc", _int, [_vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    ("corr_selftest_wait_timeout", _int, [_i32, _vp]),
     # microbenchmarks (include/xengine_peaks.h)
     ("xe_peak_imma_s8", ctypes.c_double, [_int, _vp]),
     ("xe_peak_dp4a", ctypes.c_double, [_int, _vp]),

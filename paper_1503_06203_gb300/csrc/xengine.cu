@@ -1320,3 +1320,40 @@ extern "C" int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int3
     return fail(CORR_ECUDA, "noalloc: copying the fault word: %s", cudaGetErrorString(e));
   return CORR_OK;
 }
+
+// ---- bounded-wait self test ----------------------------------------------------
+namespace {
+
+__device__ int32_t g_wait_probe_status;
+
+// Waits (bounded) on a barrier whose phase never completes: nothing arrives.
+__global__ void wait_probe_kernel(uint32_t polls) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    xe::mbar_init(&bar, 1);
+    xe::fence_barrier_init();
+  }
+  __syncthreads();
+  const bool completed = xe::mbar_wait_bounded(&bar, 0, polls);
+  if (threadIdx.x == 0) g_wait_probe_status = completed ? 0 : 1;
+}
+
+}  // namespace
+
+int corr_selftest_wait_timeout(int32_t polls, void* stream) {
+  if (polls < 1 || polls > (1 << 20)) return fail(CORR_EINVAL, "polls must be in [1, 2^20]");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int32_t unset = -1;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_wait_probe_status, &unset, sizeof unset, 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+  wait_probe_kernel<<<1, 32, 0, st>>>(static_cast<uint32_t>(polls));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "wait probe launch: %s", cudaGetErrorString(e));
+  int32_t status = unset;
+  e = cudaMemcpyFromSymbolAsync(&status, g_wait_probe_status, sizeof status, 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(CORR_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+  if (status == 1) return fail(CORR_ETIMEOUT, "device wait ran out after %d polls (expected)", polls);
+  if (status == 0) return CORR_OK;
+  return fail(CORR_ECUDA, "wait probe recorded no status");
+}

@@ -1,4 +1,6 @@
-"""Failure handling on the GPU without faulting it: host deadlines, failed allocations, bad calls."""
+"""Failure handling on the GPU without faulting it: host deadlines, failed allocations, bad calls,
+and a bounded device wait that runs out."""
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -51,3 +53,23 @@ def test_bad_frames_rejected_before_launch(xe):
         from paper_1503_06203_gb300._lib import CORR_EINVAL, lib
         assert lib().corr_accumulate(c.handle, None, None) == CORR_EINVAL
         assert c.kernel_launches == n0 and c.status() == 0
+
+
+def test_device_wait_runs_out_and_the_context_survives(xe):
+    """A bounded device wait on a barrier nothing arrives on ends with an error status (no trap,
+    no hang); correlation afterwards is still bit-exact."""
+    import torch
+    import oracle
+    import synth
+    for polls in (1, 64, 4096):
+        assert xe.selftest_wait_timeout(polls) == xe.CORR_ETIMEOUT
+    assert "ran out" in xe.last_error()
+    with pytest.raises(xe.XEngineError):
+        from paper_1503_06203_gb300 import check
+        check(xe.selftest_wait_timeout(0))  # polls outside [1, 2^20]: rejected before launch
+    x = synth.gauss(96, 2, 300, 2.5, 91)
+    with xe.Correlator(96, 2, 300) as c:
+        c.accumulate(torch.from_numpy(x).cuda())
+        V = c.readout().cpu().numpy().astype(np.int64)
+        assert c.status() == 0
+    assert np.array_equal(V, oracle.visibilities(x))
