@@ -166,6 +166,25 @@ def measured_peaks_file():
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
+def int_mm_rate(n: int = 8192, reps: int = 5) -> float:
+    """int8 x int8 -> int32 GEMM rate of the vendor library (torch._int_mm, n^3), in operations/s."""
+    import torch
+    a = torch.randint(-8, 8, (n, n), dtype=torch.int8, device="cuda")
+    b = torch.randint(-8, 8, (n, n), dtype=torch.int8, device="cuda")
+    for _ in range(2):
+        torch._int_mm(a, b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch._int_mm(a, b)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del a, b
+    return 2.0 * n ** 3 / (ms * 1e-3)
+
+
 def cpu_oracle_sample(frame, x, target_s: float, per_band_s: float | None = None):
     """Time the CPU oracle as it stands on a bounded sample: the first F_s bands of the frame.
 
@@ -293,6 +312,7 @@ def run_xengine(args, wl_key):
     mo, do = ctypes.c_double(), ctypes.c_double()
     combo = max(L.xe_peak_imma_dp4a(4000, r, sp, ctypes.byref(mo), ctypes.byref(do)) for r in (16, 24, 32))
     dp4a = L.xe_peak_dp4a(4000, sp)
+    int_mm = int_mm_rate()  # the library int8 GEMM (cuBLASLt through torch._int_mm), for context
 
     c = xe.Correlator(N, F, T)
     from paper_1503_06203_gb300 import autotune
@@ -366,6 +386,11 @@ def run_xengine(args, wl_key):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, _, _ = cpu_oracle_sample(frame, x_host.numpy(), args.cpu_seconds)
         cpu = {"value": round(v, 6), "unit": "TOPS", "cores": cores, "kind": "oracle", "sample": desc}
+        # and on one core, one band (the oracle as it stands, single-threaded)
+        import oracle
+        _, t1, _ = oracle.timed_visibilities(np.ascontiguousarray(x_host.numpy()[:, :1, :]), 1)
+        cpu["single_thread"] = {"value": round(4.0 * N * (N + 1) * T / t1 / 1e12, 6), "cores": 1,
+                                "sample": f"band 0 of the N={N} T={T} frame"}
 
     achieved = ops / (avg_kernel_ms * 1e-3) / 1e12
     product = c.get_option(xe.CORR_OPT_PRODUCT)
@@ -401,7 +426,8 @@ def run_xengine(args, wl_key):
                      "hbm_frac": round((in_bytes + out_bytes) / (avg_kernel_ms * 1e-3) / 1e9 /
                                        (measured_peaks_file() or {}).get("hbm_gbs", 6699.8), 4)},
         "peaks_tops": {"imma_s8": round(imma / 1e12, 2), "dp4a": round(dp4a / 1e12, 2),
-                       "imma_plus_dp4a": round(combo / 1e12, 2)},
+                       "imma_plus_dp4a": round(combo / 1e12, 2),
+                       "cublaslt_int8_gemm_8192": round(int_mm / 1e12, 2)},
         "e2e": {"value": round(e2e, 3), "unit": "TOPS", "h2d_bytes_per_step": in_bytes,
                 "d2h_bytes_per_step": out_bytes},
         "gpu_launches": int(launches),
