@@ -108,26 +108,40 @@ __global__ void __launch_bounds__(kLagThreads) shift_lags_kernel(const uint8_t* 
 namespace xe {
 
 // ---- streaming form: a TMA ring along time ----------------------------------
-// A CTA owns one band's block of 64 elements over a segment of `tseg` output
-// samples and walks it in blocks of 128 samples. Source rows arrive by TMA in
-// boxes of 64 elements x 128 samples (box b = rows 128b .. 128b+127) into a
-// ring of kLagRing boxes, where row s sits at ((s mod 1024) * 64). Each source
-// row is read from HBM once per segment. The block at t0 needs the boxes of
-// rows t0 - lmax .. t0 + 127 - lmin (lmin, lmax: the block's lag range), at
-// most 6 when lmax - lmin <= kLagSpanRing; box b + kLagRing replaces box b
-// once no thread reads it. Boxes are issued in order from the CTA's first
-// box, so box b is use (b - first) / kLagRing of its barrier.
+// A CTA owns one band's block of kW elements (kW = 128, or 64 for narrow
+// frames) over a segment of `tseg` output samples and walks it in blocks of
+// kBR = 8192 / kW samples. Source rows arrive by TMA in boxes of kW elements x
+// kBR samples (box b = rows kBR b .. kBR b + kBR - 1) into a 64 KiB ring of
+// kLagRing boxes, where row s sits at (s mod kRR) * kW, kRR = kLagRing kBR.
+// Each source row is read from HBM once per segment. The block at t0 needs
+// the boxes of rows t0 - lmax .. t0 + kBR - 1 - lmin (lmin, lmax: the block's
+// lag range), at most 6 when lmax - lmin <= 4 kBR; box b + kLagRing replaces
+// box b once no thread reads it. Boxes are issued in order from the CTA's
+// first box, so box b is use (b - first) / kLagRing of its barrier. Wider
+// blocks make every TMA row request and every store a whole 128-byte line.
 //
-// Shared-memory banks: a warp covers 8 rows x 4 quads of 16 bytes; lane
-// (quad q, row r) visits its quad's words starting at word r / 2, so that at
-// every step the 32 lanes read 32 different banks (rows r, r + 1 share the
-// word but their source rows differ by one, i.e. by 16 banks).
+// Shared-memory banks: a warp covers kR = 32 / kQ rows x kQ = kW / 16 quads of
+// 16 bytes; lane (quad q, row r) visits its quad's words starting at word
+// 4 r / kR, so that at every step the 32 lanes read 32 different banks. With
+// kW = 128 rows are 32 words apart and the 4 rows start at 4 different words;
+// with kW = 64 rows are 16 words apart, and rows r, r + 1 share the start
+// word but their source rows differ by one, i.e. by 16 banks.
 constexpr int kLagRing = 8;
-constexpr int kLagRingRows = kLagRing * 128;  // 1024: row s lives at (s & 1023) * 64
-constexpr int kLagSpanRing = 512;
+constexpr int kLagRingBytes = 64 * 1024;
 constexpr int kLagStreamThreads = 256;
-constexpr int kLagRingBytes = kLagRingRows * 64;  // 64 KiB
 constexpr int kLagStreamSmem = kLagRingBytes + 128;  // dynamic shared memory (aligned to 128 inside)
+
+template <int kW>
+struct LagGeom {
+  static constexpr int kBR = 8192 / kW;         // rows per box and per block
+  static constexpr int kBRLog = kW == 64 ? 7 : 6;
+  static constexpr int kRR = kLagRing * kBR;    // ring rows
+  static constexpr int kSpan = 4 * kBR;         // largest lag range the ring serves
+  static constexpr int kQ = kW / 16;            // quads per row
+  static constexpr int kR = 32 / kQ;            // rows per warp step
+  static constexpr int kPassRows = 8 * kR;      // rows per pass of the 8 warps
+  static_assert((1 << kBRLog) == kBR && kBR == 2 * kPassRows, "two passes per block");
+};
 
 struct LagStreamArgs {
   const uint8_t* in;  // the frame the map describes (for blocks with a wide lag range)
@@ -143,10 +157,10 @@ __device__ __forceinline__ int64_t clamp64(int64_t v, int64_t lo, int64_t hi) { 
 // One lane's 16 output bytes of row t (see the bank note above): visiting
 // step w reads word (w + rot) & 3 of the lane's quad; kInterior = every
 // source row of the block lies inside the frame.
-template <bool kInterior>
+template <int kW, bool kInterior>
 __device__ __forceinline__ uint4 lag_unit(const uint8_t* ring, int32_t t, const uint32_t (&c)[16],
                                           const int32_t (&lg)[16], int rot, int32_t T) {
-  const uint32_t tb = static_cast<uint32_t>(t & (kLagRingRows - 1)) * 64u;
+  const uint32_t tb = static_cast<uint32_t>(t & (LagGeom<kW>::kRR - 1)) * kW;
   uint32_t wv[4];
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
@@ -172,23 +186,25 @@ __device__ __forceinline__ uint4 lag_unit(const uint8_t* ring, int32_t t, const 
   return o;
 }
 
+template <int kW>
 __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel(const __grid_constant__ CUtensorMap map,
                                                                               const LagStreamArgs a) {
+  using G = LagGeom<kW>;
   extern __shared__ __align__(16) uint8_t dyn_smem[];
   // 128-byte aligned ring, addressed from dyn_smem so the compiler keeps shared-space loads
   uint8_t* const ring = dyn_smem + ((128u - (smem_u32(dyn_smem) & 127u)) & 127u);
   __shared__ __align__(8) uint64_t full[kLagRing];
-  __shared__ int32_t lag_s[64];
+  __shared__ int32_t lag_s[kW];
   __shared__ int32_t span[2];
   const int tid = threadIdx.x;
-  const int nblk = (a.N + 63) / 64;
+  const int nblk = (a.N + kW - 1) / kW;
   const int eb = static_cast<int>(blockIdx.x % nblk);
   const int rest = static_cast<int>(blockIdx.x / nblk);
   const int f = rest % a.F;
   const int64_t t_begin = static_cast<int64_t>(rest / a.F) * a.tseg;
   const int64_t t_end = min(static_cast<int64_t>(a.T), t_begin + a.tseg);
-  const int i0 = eb * 64;
-  const int ne = min(64, a.N - i0);  // a multiple of 16 (N % 16 == 0)
+  const int i0 = eb * kW;
+  const int ne = min(kW, a.N - i0);  // a multiple of 16 (N % 16 == 0)
   if (tid == 0) {
     span[0] = INT32_MAX;
     span[1] = INT32_MIN;
@@ -196,7 +212,7 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
     fence_barrier_init();
   }
   __syncthreads();
-  if (tid < 64) {
+  if (tid < kW) {
     const int32_t l = tid < ne ? a.lags[i0 + tid] : 0;
     lag_s[tid] = l;
     if (tid < ne) {
@@ -207,10 +223,10 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
   __syncthreads();
   const int64_t lmin = span[0], lmax = span[1];
   const int64_t row_stride = static_cast<int64_t>(a.F) * a.N;
-  if (lmax - lmin > kLagSpanRing) {  // too wide for the ring: gather bytes from global memory
-    for (int64_t k = tid; k < (t_end - t_begin) * 16; k += kLagStreamThreads) {
-      const int64_t t = t_begin + (k >> 4);
-      const int e0 = static_cast<int>(k & 15) * 4;
+  if (lmax - lmin > G::kSpan) {  // too wide for the ring: gather bytes from global memory
+    for (int64_t k = tid; k < (t_end - t_begin) * (kW / 4); k += kLagStreamThreads) {
+      const int64_t t = t_begin + k / (kW / 4);
+      const int e0 = static_cast<int>(k % (kW / 4)) * 4;
       if (e0 >= ne) continue;
       uint32_t word = 0;
       for (int u = 0; u < 4; ++u) {
@@ -226,13 +242,13 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
   const int64_t s_lo = max(int64_t(0), t_begin - lmax);
   const int64_t s_hi = min(static_cast<int64_t>(a.T) - 1, t_end - 1 - lmin);
   const bool any = s_lo <= s_hi;
-  const int64_t first = s_lo >> 7, last = s_hi >> 7;
+  const int64_t first = s_lo >> G::kBRLog, last = s_hi >> G::kBRLog;
 
   // this lane's quad, rows and rotated word order
   const int lane = tid & 31, warp = tid >> 5;
-  const int q = lane & 3, rr = lane >> 2;  // rows rr and rr + 8 of each warp's 16
-  const int rot = rr >> 1;
-  uint32_t c[16];  // (e - 64 * lag) mod 2^32 for the lane's 16 elements in visiting order
+  const int q = lane % G::kQ, rr = lane / G::kQ;  // rows warp kR + rr and that + kPassRows of each block
+  const int rot = rr * 4 / G::kR;
+  uint32_t c[16];  // (e - kW lag) mod 2^32 for the lane's 16 elements in visiting order
   int32_t lg[16];
 #pragma unroll
   for (int w = 0; w < 4; ++w)
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
     for (int b = 0; b < 4; ++b) {
       const int e = 16 * q + 4 * ((w + rot) & 3) + b;
       lg[4 * w + b] = lag_s[e];
-      c[4 * w + b] = static_cast<uint32_t>(e) - 64u * static_cast<uint32_t>(lag_s[e]);
+      c[4 * w + b] = static_cast<uint32_t>(e) - static_cast<uint32_t>(kW) * static_cast<uint32_t>(lag_s[e]);
     }
   const bool quad_live = 16 * q < ne;
   uint8_t* out_base = a.out + static_cast<int64_t>(f) * a.N + i0 + 16 * q;
@@ -250,8 +266,8 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
     lim = min(lim, last);
     for (; next <= lim; ++next) {
       uint64_t* bar = &full[next % kLagRing];
-      mbar_arrive_expect_tx(bar, 64u * 128u);
-      tma_load_3d(ring + (next % kLagRing) * (128 * 64), &map, bar, i0, f, static_cast<int32_t>(next * 128));
+      mbar_arrive_expect_tx(bar, static_cast<uint32_t>(kW * G::kBR));
+      tma_load_3d(ring + (next % kLagRing) * (kW * G::kBR), &map, bar, i0, f, static_cast<int32_t>(next * G::kBR));
     }
   };
   if (tid == 0 && any) {
@@ -259,12 +275,12 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
     issue_upto(first + kLagRing - 1);
   }
   bool fault = false;
-  for (int64_t t0 = t_begin; t0 < t_end; t0 += 128) {
+  for (int64_t t0 = t_begin; t0 < t_end; t0 += G::kBR) {
     int64_t lo = 0;
     bool ok = true;
     if (any) {
-      lo = clamp64((t0 - lmax) >> 7, first, last);
-      const int64_t hi = clamp64((t0 + 127 - lmin) >> 7, first, last);
+      lo = clamp64((t0 - lmax) >> G::kBRLog, first, last);
+      const int64_t hi = clamp64((t0 + G::kBR - 1 - lmin) >> G::kBRLog, first, last);
       for (int64_t b = lo; b <= hi && ok; ++b)
         ok = mbar_wait_bounded(&full[b % kLagRing], static_cast<uint32_t>(((b - first) / kLagRing) & 1), kSpinLimit);
     }
@@ -274,12 +290,13 @@ __global__ void __launch_bounds__(kLagStreamThreads, 3) shift_lags_stream_kernel
     }
     // every thread is past the previous block: boxes below lo are free
     if (tid == 0 && any) issue_upto(lo + kLagRing - 1);
-    const bool interior = t0 - lmax >= 0 && t0 + 127 - lmin < a.T;
+    const bool interior = t0 - lmax >= 0 && t0 + G::kBR - 1 - lmin < a.T;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int32_t tt = static_cast<int32_t>(t0) + warp * 16 + rr + 8 * h;
+      const int32_t tt = static_cast<int32_t>(t0) + h * G::kPassRows + warp * G::kR + rr;
       if (tt >= t_end || !quad_live) continue;
-      const uint4 o = interior ? lag_unit<true>(ring, tt, c, lg, rot, a.T) : lag_unit<false>(ring, tt, c, lg, rot, a.T);
+      const uint4 o = interior ? lag_unit<kW, true>(ring, tt, c, lg, rot, a.T)
+                               : lag_unit<kW, false>(ring, tt, c, lg, rot, a.T);
       *reinterpret_cast<uint4*>(out_base + static_cast<int64_t>(tt) * row_stride) = o;
     }
   }

@@ -273,12 +273,13 @@ void free_plan(Plan* pl) {
   *pl = Plan();
 }
 
-int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_t T) {
+int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_t T, uint32_t box_n = xe::kTile,
+              uint32_t box_t = xe::kTC) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CORR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(F), static_cast<cuuint64_t>(T)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(Np) * static_cast<cuuint64_t>(F)};
-  cuuint32_t box[3] = {static_cast<cuuint32_t>(xe::kTile), 1u, static_cast<cuuint32_t>(xe::kTC)};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(box_n), 1u, static_cast<cuuint32_t>(box_t)};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1000,13 +1001,16 @@ int lag_stream_setup(int dev) {
     if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e));
   }
   if (!g_lag_ctas_per_sm[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(xe::shift_lags_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         xe::kLagStreamSmem);
-    if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, xe::shift_lags_stream_kernel, xe::kLagStreamThreads,
-                                                      xe::kLagStreamSmem);
-    if (e != cudaSuccess || bps < 1) return fail(CORR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+    int bps = 1 << 30;
+    for (const void* k : {reinterpret_cast<const void*>(xe::shift_lags_stream_kernel<64>),
+                          reinterpret_cast<const void*>(xe::shift_lags_stream_kernel<128>)}) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, xe::kLagStreamSmem);
+      if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+      int b = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, xe::kLagStreamThreads, xe::kLagStreamSmem);
+      if (e != cudaSuccess || b < 1) return fail(CORR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+      bps = std::min(bps, b);
+    }
     g_lag_ctas_per_sm[dev] = bps;
   }
   return CORR_OK;
@@ -1036,7 +1040,8 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
     if (rc) return rc;
     // segments of the time axis: about 8 waves of CTAs, each segment at least
     // 1024 samples (its boundary re-reads the lag range once)
-    const int64_t units = ceil_div(N, 64) * F;
+    const int kw = N >= 128 ? 128 : 64;  // element block width (see xe_lags.cuh)
+    const int64_t units = ceil_div(N, kw) * F;
     const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_lag_ctas_per_sm[dev];
     const int64_t nseg_want = std::max<int64_t>(1, ceil_div(8 * slots, units));
     int64_t tseg = ceil_div(ceil_div(T, nseg_want), 128) * 128;
@@ -1044,10 +1049,13 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
     const int64_t ctas = units * ceil_div(T, tseg);
     if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");
     CUtensorMap tm;
-    rc = make_tmap(&tm, in_dev, N, F, T);
+    rc = make_tmap(&tm, in_dev, N, F, T, static_cast<uint32_t>(kw), static_cast<uint32_t>(8192 / kw));
     if (rc) return rc;
     xe::LagStreamArgs la{in_dev, out_dev, lags_dev, N, F, T, static_cast<int32_t>(tseg), g_lag_err_dev};
-    xe::shift_lags_stream_kernel<<<static_cast<unsigned>(ctas), xe::kLagStreamThreads, xe::kLagStreamSmem, st>>>(tm, la);
+    if (kw == 128)
+      xe::shift_lags_stream_kernel<128><<<static_cast<unsigned>(ctas), xe::kLagStreamThreads, xe::kLagStreamSmem, st>>>(tm, la);
+    else
+      xe::shift_lags_stream_kernel<64><<<static_cast<unsigned>(ctas), xe::kLagStreamThreads, xe::kLagStreamSmem, st>>>(tm, la);
   } else {
     const int64_t ctas = ceil_div(N, 64) * F * ceil_div(T, xe::kLagTB);
     if (ctas > INT32_MAX) return fail(CORR_EINVAL, "shift_lags: frame too large");

@@ -50,6 +50,11 @@ def _lag_case(kind, N, T, rng):
         if N > 65:
             lags[64], lags[65] = -257, 256
         return lags
+    if kind == "span_limit_wide":  # 128-element blocks: block 0 spans exactly the ring's 256 samples, block 1 one more
+        lags = rng.integers(-100, 100, N)
+        lags[0], lags[1] = -128, 128
+        lags[128], lags[129] = -129, 128
+        return lags
     if kind == "const_pos":
         return np.full(N, 300)
     if kind == "beyond_pos":
@@ -66,13 +71,16 @@ def _lag_case(kind, N, T, rng):
     raise ValueError(kind)
 
 
-# Streaming (TMA ring) path: N % 16 == 0 and 16-byte aligned buffers. The cases
-# cover a ragged element block (N = 80), ragged T, several time segments
-# (T = 8192), the ring's lag-range limit and one past it, constant lags,
-# elements shifted out entirely and the int32 ends of the lag range.
+# Streaming (TMA ring) path: N % 16 == 0 and 16-byte aligned buffers; blocks of
+# 64 elements below N = 128, of 128 from there. The cases cover ragged element
+# blocks (N = 80, 176), ragged T, several time segments (T = 8192), each
+# width's lag-range limit and one past it, constant lags, elements shifted out
+# entirely and the int32 ends of the lag range.
 @pytest.mark.parametrize("N,F,T,kind", [
     (80, 3, 1000, "uniform100"),
-    (128, 2, 3000, "span_limit"),
+    (64, 2, 3000, "span_limit"),
+    (256, 2, 3000, "span_limit_wide"),
+    (176, 3, 1500, "uniform100"),
     (64, 1, 5000, "const_pos"),
     (64, 2, 700, "beyond_pos"),
     (64, 2, 700, "beyond_neg"),
