@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["xengine", "reference"], default="xengine")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(EXTRA_WORKLOADS), default="pathfinder")
-    ap.add_argument("--rates", default="10,25,40", help="served: Poisson arrival rates (frames/s) to sweep")
+    ap.add_argument("--rates", default="10,25,40,60,80", help="served: Poisson arrival rates (frames/s) to sweep")
     ap.add_argument("--served-frames", type=int, default=160, help="served: frames per rate")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -509,8 +509,10 @@ def run_served(args):
     budget = 24 << 30
     srv = serve.Server(specs, t_max, pool, budget_bytes=budget, readout_every=16)
     sweeps = []
-    for k, rate in enumerate(float(r) for r in args.rates.split(",")):
-        arr = serve.poisson_arrivals(rate, args.served_frames, len(specs), t_min, t_max, pool_bytes, specs, 1004 + k)
+    for rate in (float(r) for r in args.rates.split(",")):
+        # seeded by the rate itself, so a rate gets the same arrivals in any sweep
+        arr = serve.poisson_arrivals(rate, args.served_frames, len(specs), t_min, t_max, pool_bytes, specs,
+                                     1004000 + int(round(10 * rate)))
         out = {"rate_hz": rate}
         for mode in ("served", "plain"):
             srv.reset()

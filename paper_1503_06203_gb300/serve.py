@@ -8,7 +8,7 @@ out every `readout_every` frames, which starts the next integration
 (Sec. II.A: products are accumulated over many samples).
 
 The server admits arriving frames while their input bytes fit a device-
-memory budget (a ring inside one preallocated slab), copies each admitted
+memory budget (first-fit blocks inside one preallocated slab), copies each admitted
 frame to the device on a copy stream, and launches every copied frame not
 yet correlated in one batched launch (at most one frame per stream per
 launch: a stream's frames add into the same accumulators in arrival
@@ -21,6 +21,7 @@ correlation runs in the CUDA library.
 """
 from __future__ import annotations
 
+import bisect
 import collections
 import time
 from dataclasses import dataclass, field
@@ -84,59 +85,50 @@ def poisson_arrivals(rate_hz: float, count: int, streams: int, t_min: int, t_max
     return out
 
 
-class RingSlab:
-    """First-in-first-out allocator inside one device buffer: the in-flight input budget.
+class SlabAllocator:
+    """First-fit allocator inside one device buffer: the in-flight input budget.
 
-    The live region is one circular span [tail, head). A frame may finish
-    before frames admitted earlier (a stream's next frame waits for the
-    stream's current one); its space is marked free and reclaimed once every
-    older frame is done too.
+    Frames may finish in any order (a stream's next frame waits for the
+    stream's current one). A freed block is merged with its free neighbours
+    at once, so a frame still waiting behind its stream's earlier frames does
+    not hold up the space of frames that already finished.
     """
 
     def __init__(self, nbytes: int, device: str | None = "cuda"):
         # device=None keeps only the bookkeeping (host-side tests)
         self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device) if device else None
         self.size = nbytes
-        self.head = 0
-        self.live = collections.deque()  # [start, end, freed], oldest first
+        self.free_blocks = [[0, nbytes]]  # [start, end), sorted by start, never adjacent
+        self.live = {}                    # start -> end
         self.used = 0
 
     def alloc(self, nbytes: int):
         nbytes = (nbytes + 255) // 256 * 256
         if nbytes > self.size:
             raise ValueError("frame larger than the device-memory budget")
-        if not self.live:
-            start = 0
-        else:
-            tail = self.live[0][0]
-            if self.head > tail:  # free: [head, size) and [0, tail)
-                if self.head + nbytes <= self.size:
-                    start = self.head
-                elif nbytes <= tail:
-                    start = 0
+        for k, (s, e) in enumerate(self.free_blocks):
+            if e - s >= nbytes:
+                if e - s == nbytes:
+                    del self.free_blocks[k]
                 else:
-                    return None
-            elif self.head + nbytes <= tail:  # wrapped: free [head, tail)
-                start = self.head
-            else:
-                return None
-        self.live.append([start, start + nbytes, False])
-        self.head = start + nbytes
-        self.used += nbytes
-        return start
+                    self.free_blocks[k][0] = s + nbytes
+                self.live[s] = s + nbytes
+                self.used += nbytes
+                return s
+        return None
 
     def free(self, start: int):
-        for entry in self.live:
-            if entry[0] == start and not entry[2]:
-                entry[2] = True
-                break
-        else:
-            raise KeyError(start)
-        while self.live and self.live[0][2]:
-            s, e, _ = self.live.popleft()
-            self.used -= e - s
-        if not self.live:
-            self.head = 0
+        end = self.live.pop(start)  # KeyError for a block that is not live
+        self.used -= end - start
+        starts = [b[0] for b in self.free_blocks]
+        k = bisect.bisect_left(starts, start)
+        self.free_blocks.insert(k, [start, end])
+        if k + 1 < len(self.free_blocks) and self.free_blocks[k + 1][0] == end:  # merge right
+            self.free_blocks[k][1] = self.free_blocks[k + 1][1]
+            del self.free_blocks[k + 1]
+        if k > 0 and self.free_blocks[k - 1][1] == start:  # merge left
+            self.free_blocks[k - 1][1] = self.free_blocks[k][1]
+            del self.free_blocks[k]
 
 
 class Server:
@@ -153,7 +145,7 @@ class Server:
         self.readouts = [[] for _ in specs]  # host copies of every readout (for checks), optional
         self.keep_readouts = False
         self.counts = [0] * len(specs)
-        self.ring = RingSlab(budget_bytes)
+        self.ring = SlabAllocator(budget_bytes)
         self.copy_stream = torch.cuda.Stream()
         self.compute_stream = torch.cuda.Stream()
 

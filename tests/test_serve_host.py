@@ -1,4 +1,4 @@
-"""Host logic of the serving loop (no GPU): the in-flight budget ring and the arrival recipe."""
+"""Host logic of the serving loop (no GPU): the in-flight budget allocator and the arrival recipe."""
 import random
 
 import pytest
@@ -8,8 +8,8 @@ pytest.importorskip("torch")
 from paper_1503_06203_gb300 import serve  # noqa: E402
 
 
-def test_ring_never_overlaps_live_frames():
-    r = serve.RingSlab(10000, device=None)
+def test_slab_never_overlaps_live_frames():
+    r = serve.SlabAllocator(10000, device=None)
     rnd = random.Random(3)
     held = []
     for _ in range(30000):
@@ -26,17 +26,30 @@ def test_ring_never_overlaps_live_frames():
             r.free(a)
     for a, _ in held:
         r.free(a)
-    assert r.used == 0 and r.head == 0
+    assert r.used == 0 and r.free_blocks == [[0, r.size]]
 
 
-def test_ring_respects_budget():
-    r = serve.RingSlab(4096, device=None)
+def test_slab_respects_budget():
+    r = serve.SlabAllocator(4096, device=None)
     assert r.alloc(4096) == 0
     assert r.alloc(1) is None
     r.free(0)
     assert r.alloc(2048) == 0 and r.alloc(2048) == 2048 and r.alloc(256) is None
     with pytest.raises(ValueError):
         r.alloc(5000)
+
+
+def test_slab_reuses_space_freed_out_of_order():
+    """A block freed while an older one is still live is reusable at once (no head-of-line blocking)."""
+    r = serve.SlabAllocator(3 * 256, device=None)
+    a, b, c = r.alloc(256), r.alloc(256), r.alloc(256)
+    assert (a, b, c) == (0, 256, 512) and r.alloc(1) is None
+    r.free(b)                  # the middle frame finishes first
+    assert r.alloc(256) == b   # its space is taken at once
+    r.free(a)
+    r.free(c)
+    r.free(b)
+    assert r.free_blocks == [[0, 768]] and r.used == 0
 
 
 def test_poisson_arrivals_recipe():
