@@ -1,20 +1,30 @@
 #!/usr/bin/env python
-"""Benchmark of the GB300 4-bit X-engine: effective TOPS on one correlation frame.
+"""Benchmark of the GB300 4-bit X-engine: effective TOPS on one correlation frame, with the
+other workloads of the hot path as sub-records of the same line.
 
 One step = one pass of the whole hot path over one frame of synthetic
 4-bit input already resident in HBM: TMA staging, unpack, Hermitian
 product, upper-triangle scheduling and the packed-triangle write of the
-visibilities (a fresh integration each step). The workload is the
+visibilities (a fresh integration each step). The headline workload is the
 Pathfinder shape, N=256 elements, F=256 bands, T=16384 samples per
 integration (1 GiB of input, larger than L2, so no flush is needed).
 
 Effective operations follow Eq. 2 of the paper: 4 N (N+1) F T per frame.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xengine|reference]
+The default single-GPU run adds, in the same JSON line:
+  large_n     the N=8192, F=4, T=2048 frame (roofline, CPU-oracle sample, e2e);
+  batched     64 uneven frames: one batched launch per step vs one launch per frame;
+  served      32 served streams, Poisson arrivals at 10, 40 and 80 frames/s:
+              continuous batching vs one frame per launch (frames/s, p50/p99);
+  lags_gates  the Sec. IV lag shift (GB/s vs HBM) and gated correlation.
 
-Under torchrun (N > 1) every rank correlates its own frame (bands are
-independent, Sec. I), there is no collective on the data path, and the
-reported value is all ranks' operations over the slowest rank's time.
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xengine|reference] [--split frames|bands]
+
+Under torchrun (N > 1) there is no collective on the data path: with
+--split frames (the default) every rank correlates its own frame (weak
+scaling); with --split bands the ranks share one frame and each correlates
+its range of bands (strong scaling; bands are independent, Sec. I and IV).
+The value is all ranks' operations over the slowest rank's time.
 ``--impl reference`` times the CPU oracle (the plain definition) on a
 bounded sample of the same workload on the host cores.
 """
@@ -41,8 +51,10 @@ WORKLOADS = {
 EXTRA_WORKLOADS = ("batched", "served", "lags_gates")
 KERNEL_NAME = "corr_tile_kernel"
 KERNEL_SOURCES = ["paper_1503_06203_gb300/csrc/xe_corr.cuh", "paper_1503_06203_gb300/csrc/xe_ptx.cuh"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "corr_tile_kernel_pathfinder.md")
+TRAFFIC_FILES = {"pathfinder": os.path.join(ROOT, "profiles", "corr_tile_kernel_pathfinder.md"),
+                 "large_n": os.path.join(ROOT, "profiles", "corr_tile_kernel_large_n.md")}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SERVED_RATES = "10,40,80"
 
 
 def parse_args():
@@ -52,13 +64,18 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["xengine", "reference"], default="xengine")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + list(EXTRA_WORKLOADS), default="pathfinder")
-    ap.add_argument("--rates", default="10,25,40,60,80", help="served: Poisson arrival rates (frames/s) to sweep")
-    ap.add_argument("--served-frames", type=int, default=160, help="served: frames per rate")
+    ap.add_argument("--split", choices=["frames", "bands"], default="frames",
+                    help="N > 1: each rank its own frame (weak scaling) or its bands of one frame (strong scaling)")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only (no sub-records)")
+    ap.add_argument("--rates", default=SERVED_RATES, help="served: Poisson arrival rates (frames/s) to sweep")
+    ap.add_argument("--served-frames", type=int, default=0, help="served: frames per rate (0: about 6 s of arrivals)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch knobs (profiling runs)")
     ap.add_argument("--product", type=int, choices=[0, 1, 2], default=None,
                     help="force the product path (0 tensor cores, 1 tensor cores + dp4a, 2 offset-encoded operands)")
+    ap.add_argument("--mma-steps", type=int, choices=[4, 5, 6, 7, 8], default=None,
+                    help="force the tensor-core share: k-steps of every 8 on the tensor cores, the rest on dp4a")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -121,20 +138,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str, product: int, split: int):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source
-    with the same launch knobs (a time split changes the writers' traffic)."""
-    if not os.path.exists(TRAFFIC_FILE):
+def recorded_traffic(workload: str, product: int, split: int, mma_steps: int):
+    """DRAM bytes per launch from the committed ncu summary of this workload, if taken on the current
+    kernel source with the same launch knobs (a time split changes the writers' traffic)."""
+    path = TRAFFIC_FILES.get(workload)
+    if not path or not os.path.exists(path):
         return None
     vals = {}
-    with open(TRAFFIC_FILE) as fh:
+    with open(path) as fh:
         for line in fh:
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256_16") != kernel_source_hash() or vals.get("workload") != workload:
         return None
-    if vals.get("options") != f"product={product} split={split}":
+    if vals.get("options") != f"product={product} split={split} mma_steps={mma_steps}":
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -185,10 +203,11 @@ def int_mm_rate(n: int = 8192, reps: int = 5) -> float:
     return 2.0 * n ** 3 / (ms * 1e-3)
 
 
-def cpu_oracle_sample(frame, x, target_s: float, per_band_s: float | None = None):
+def cpu_oracle_sample(frame, x, target_s: float, per_band_s: float | None = None, bands: int | None = None):
     """Time the CPU oracle as it stands on a bounded sample: the first F_s bands of the frame.
 
-    F_s is chosen so the sample takes about target_s (from per_band_s, measured on 2 bands if None).
+    F_s is `bands` if given, else chosen so the sample takes about target_s (from per_band_s,
+    measured on up to 2 bands if None).
     Returns (effective TOPS, cores, sample description, seconds, per-band seconds).
     """
     import numpy as np
@@ -196,11 +215,14 @@ def cpu_oracle_sample(frame, x, target_s: float, per_band_s: float | None = None
     import oracle
 
     n = oracle.threads()
-    if per_band_s is None:
-        F_cal = max(1, min(frame.F, 2))
-        _, t_cal, _ = oracle.timed_visibilities(np.ascontiguousarray(x[:, :F_cal, :]), n)
-        per_band_s = max(t_cal / F_cal, 1e-6)
-    F_s = int(max(1, min(frame.F, round(target_s / per_band_s))))
+    if bands is not None:
+        F_s = int(max(1, min(frame.F, bands)))
+    else:
+        if per_band_s is None:
+            F_cal = max(1, min(frame.F, 2))
+            _, t_cal, _ = oracle.timed_visibilities(np.ascontiguousarray(x[:, :F_cal, :]), n)
+            per_band_s = max(t_cal / F_cal, 1e-6)
+        F_s = int(max(1, min(frame.F, round(target_s / per_band_s))))
     xs = np.ascontiguousarray(x[:, :F_s, :])
     _, t, n = oracle.timed_visibilities(xs, n)
     ops = 4.0 * frame.N * (frame.N + 1) * F_s * frame.T
@@ -279,56 +301,67 @@ def aggregate_tops(world: int, ops_per_frame: float, steps: int, max_ms: float) 
     return world * ops_per_frame * steps / (max_ms * 1e-3) / 1e12
 
 
-def run_xengine(args, wl_key):
+def measure_peaks(L, sp) -> dict:
+    """Integer-pipe peaks of this GPU, measured now (the roofline denominators), in operations/s."""
     import ctypes
-    import dataclasses
+    imma = L.xe_peak_imma_s8(4000, sp)
+    mo, do = ctypes.c_double(), ctypes.c_double()
+    combo = max(L.xe_peak_imma_dp4a(4000, r, sp, ctypes.byref(mo), ctypes.byref(do)) for r in (16, 24, 32))
+    dp4a = L.xe_peak_dp4a(4000, sp)
+    return {"imma": imma, "combo": combo, "dp4a": dp4a, "int_mm": int_mm_rate()}
 
-    import numpy as np
+
+def h2d_rate(x_host, x_dev) -> float:
+    """This machine's host-to-device copy rate from pinned memory, GB/s (context for the e2e figure)."""
     import torch
-
-    import paper_1503_06203_gb300 as xe
-    import synth
-    from paper_1503_06203_gb300._lib import lib
-
-    rank, world, local = _dist_setup()
-    torch.cuda.set_device(local)
-    xe.build()
-    L = lib()
-    base = getattr(synth, WORKLOADS[wl_key][0])
-    frame = rank_frame(base, rank)
-    N, F, T = frame.N, frame.F, frame.T
-    ops = 4.0 * N * (N + 1) * F * T
-    in_bytes = N * F * T
-    out_bytes = F * xe.baselines(N) * 2 * 4
-
-    x_host = torch.empty((T, F, N), dtype=torch.uint8).pin_memory()
-    frame.make(out=x_host.numpy())
-    x_dev = x_host.to("cuda", non_blocking=False)
-    # this machine's host-to-device copy rate from pinned memory (context for the e2e figure)
+    x_dev.copy_(x_host, non_blocking=True)
+    torch.cuda.synchronize()
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     h0.record()
     for _ in range(3):
         x_dev.copy_(x_host, non_blocking=True)
     h1.record()
     torch.cuda.synchronize()
-    h2d_gbs = 3 * x_host.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9
-    stream = torch.cuda.current_stream()
-    sp = ctypes.c_void_p(stream.cuda_stream)
+    return 3 * x_host.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9
 
-    # integer-pipe peaks of this GPU, measured now (the roofline denominators)
-    imma = L.xe_peak_imma_s8(4000, sp)
-    mo, do = ctypes.c_double(), ctypes.c_double()
-    combo = max(L.xe_peak_imma_dp4a(4000, r, sp, ctypes.byref(mo), ctypes.byref(do)) for r in (16, 24, 32))
-    dp4a = L.xe_peak_dp4a(4000, sp)
-    int_mm = int_mm_rate()  # the library int8 GEMM (cuBLASLt through torch._int_mm), for context
 
-    c = xe.Correlator(N, F, T)
+def single_frame_record(args, wl_key, frame, peaks, rank=0, world=1, bands=None, local=0, cpu=True,
+                        cpu_bands=None, job_ops=None):
+    """Time one frame per launch on resident input (the K timed steps), then end to end through the
+    public API with host buffers; check sampled visibilities against the oracle; roofline and CPU leg.
+
+    bands=(f0, f1): this rank correlates only those bands of the frame (corr_create_bands).
+    job_ops: operations of one step of the whole job (all ranks), for the e2e figure (default world x ours).
+    Returns (record dict, max over ranks of the timed region in ms, timed-region ops of this rank).
+    """
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1503_06203_gb300 as xe
     from paper_1503_06203_gb300 import autotune
+
+    N, F, T = frame.N, frame.F, frame.T
+    f0, f1 = bands if bands is not None else (0, F)
+    Fb = f1 - f0
+    ops = 4.0 * N * (N + 1) * Fb * T
+    in_bytes = N * Fb * T
+    out_bytes = Fb * xe.baselines(N) * 2 * 4
+    stream = torch.cuda.current_stream()
+    x_host = torch.empty((T, F, N), dtype=torch.uint8).pin_memory()
+    frame.make(out=x_host.numpy())
+    x_dev = torch.empty((T, F, N), dtype=torch.uint8, device="cuda")
+    h2d_gbs = h2d_rate(x_host, x_dev)
+
+    c = xe.Correlator(N, F, T, bands=bands)
     # knobs for this shape on this GPU (tuned once, outside the timed region)
     tuned = {"note": "library defaults"} if args.no_tune else autotune.apply(c)
     if args.product is not None:
         c.set_option(xe.CORR_OPT_PRODUCT, args.product)
         tuned = dict(tuned or {}, product=args.product, forced=True)
+    if args.mma_steps is not None:
+        c.set_option(xe.CORR_OPT_MMA_STEPS, args.mma_steps)
+        tuned = dict(tuned or {}, mma_steps=args.mma_steps, forced=True)
     sampler = ClockSampler(local).start()
     for _ in range(args.warmup):
         c.reset()
@@ -353,26 +386,24 @@ def run_xengine(args, wl_key):
     launches = c.kernel_launches - launches0
     if c.status() != 0:
         raise RuntimeError(f"device status {c.status()}: {xe.last_error()}")
-    elapsed_ms = t_start.elapsed_time(t_end)
-    max_ms = _max_over_ranks(world, elapsed_ms)
+    max_ms = _max_over_ranks(world, t_start.elapsed_time(t_end))
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
     avg_kernel_ms = sum(kernel_ms) / len(kernel_ms)
-    value = aggregate_tops(world, ops, args.steps, max_ms)
 
-    # spot-check the last device result against the oracle (a few entries)
+    # spot-check the last device result against the oracle: entries at tile edges and at random
     V = c.readout().cpu().numpy()
-    import oracle
     rng = np.random.default_rng(rank)
-    fi = rng.integers(0, F, 64)
-    ii = rng.integers(0, N, 64)
-    jj = rng.integers(0, N, 64)
+    K = 64
+    fi = rng.integers(0, Fb, K)
+    ii = np.concatenate([rng.integers(0, N, K - 2), [0, N - 1]])
+    jj = np.concatenate([rng.integers(0, N, K - 2), [N - 1, N - 1]])
     ii, jj = np.minimum(ii, jj), np.maximum(ii, jj)
-    ref = oracle.entries(x_host.numpy(), np.stack([fi, ii, jj], 1))
+    ref = oracle.entries(x_host.numpy(), np.stack([fi + f0, ii, jj], 1))
     if not np.array_equal(V[fi, xe.packed_index(N, ii, jj)].astype(np.int64), ref):
-        raise RuntimeError("benchmark result differs from the oracle")
+        raise RuntimeError(f"{wl_key}: result differs from the oracle")
 
     # end to end through the public API: host frame in (pinned), visibilities out (pinned)
-    out_host = torch.empty((F, xe.baselines(N), 2), dtype=torch.int32).pin_memory()
+    out_host = torch.empty((Fb, xe.baselines(N), 2), dtype=torch.int32).pin_memory()
     for _ in range(2):
         c.accumulate_host(x_host)
         c.readout_host(out_host, reset=True)
@@ -386,37 +417,34 @@ def run_xengine(args, wl_key):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = _max_over_ranks(world, e0.elapsed_time(e1))
-    e2e = world * ops * args.e2e_steps / (e2e_ms * 1e-3) / 1e12
     if not np.array_equal(out_host.numpy()[fi, xe.packed_index(N, ii, jj)].astype(np.int64), ref):
-        raise RuntimeError("end-to-end result differs from the oracle")
+        raise RuntimeError(f"{wl_key}: end-to-end result differs from the oracle")
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, desc, _, _ = cpu_oracle_sample(frame, x_host.numpy(), args.cpu_seconds)
-        cpu = {"value": round(v, 6), "unit": "TOPS", "cores": cores, "kind": "oracle", "sample": desc}
-        # and on one core, one band (the oracle as it stands, single-threaded)
-        import oracle
-        _, t1, _ = oracle.timed_visibilities(np.ascontiguousarray(x_host.numpy()[:, :1, :]), 1)
-        cpu["single_thread"] = {"value": round(4.0 * N * (N + 1) * T / t1 / 1e12, 6), "cores": 1,
-                                "sample": f"band 0 of the N={N} T={T} frame"}
+    cpu_rec = None
+    if cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, _, _ = cpu_oracle_sample(frame, x_host.numpy(), args.cpu_seconds, bands=cpu_bands)
+        cpu_rec = {"value": round(v, 6), "unit": "TOPS", "cores": cores, "kind": "oracle", "sample": desc}
+        if wl_key == "pathfinder":  # and on one core, one band (the oracle as it stands, single-threaded)
+            _, t1, _ = oracle.timed_visibilities(np.ascontiguousarray(x_host.numpy()[:, :1, :]), 1)
+            cpu_rec["single_thread"] = {"value": round(4.0 * N * (N + 1) * T / t1 / 1e12, 6), "cores": 1,
+                                        "sample": f"band 0 of the N={N} T={T} frame"}
 
     achieved = ops / (avg_kernel_ms * 1e-3) / 1e12
     product = c.get_option(xe.CORR_OPT_PRODUCT)
-    hybrid = product != 0  # paths 1 and 2 both run tensor cores and dp4a side by side
-    # the kernel's pipes: tensor cores and dp4a side by side (default), or tensor cores alone
-    peak = (combo if hybrid else imma) / 1e12
-    hw_ops = hardware_ops(N, F, T)
+    mma_steps = c.get_option(xe.CORR_OPT_MMA_STEPS)
+    split = c.get_option(xe.CORR_OPT_SPLIT)
+    hybrid = product != 0 and mma_steps < 8  # tensor cores and dp4a side by side
+    peak = (peaks["combo"] if hybrid else peaks["imma"]) / 1e12
+    hw_ops = hardware_ops(N, Fb, T)
     hw_tops = hw_ops / (avg_kernel_ms * 1e-3) / 1e12
-    traffic = recorded_traffic(wl_key, c.get_option(xe.CORR_OPT_PRODUCT), c.get_option(xe.CORR_OPT_SPLIT))
-    line = {
-        "metric": "Effective TOPS", "value": round(value, 3), "unit": "TOPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "s8 x s8 -> s32",
-        "data": "synthetic (seeded generator, paper's shapes)",
-        "config": {"workload": WORKLOADS[wl_key][1], "N": N, "F": F, "T": T, "frames_per_step": 1,
-                   "input_bytes": in_bytes, "output_bytes": out_bytes,
-                   "l2": "inputs larger than L2 (1 GiB frame), no flush" if in_bytes > 129e6 else "flush: none",
-                   "parallelism": f"one frame per rank, dp{world}" if world > 1 else "single GPU",
+    traffic = recorded_traffic(wl_key, product, split, mma_steps) if bands is None or Fb == F else None
+    hbm = (measured_peaks_file() or {}).get("hbm_gbs", 6699.8)
+    rec = {
+        "value": None, "ms_per_step": round(max_ms / args.steps, 4),
+        "config": {"workload": WORKLOADS[wl_key][1], "N": N, "F": F, "T": T, "bands": [f0, f1],
+                   "frames_per_step": 1, "input_bytes": in_bytes, "output_bytes": out_bytes,
+                   "l2": ("inputs larger than L2, no flush" if in_bytes > 129e6 else
+                          "input smaller than L2: output writes larger than L2 dominate, no flush"),
                    "tuned": {k: v for k, v in (tuned or {}).items() if k != "trials"}},
         "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TOPS",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -425,43 +453,104 @@ def run_xengine(args, wl_key):
                                         if hybrid else "mma.sync m16n8k32 s8")),
                      "product_path": {0: "tensor cores", 1: "tensor cores + dp4a",
                                       2: "tensor cores + dp4a on offset-encoded operands (Eq. 3 route)"}[product],
+                     "mma_steps_of_8": mma_steps if product != 0 else 8,
                      "note": "achieved counts Eq. 2 operations (8 per complex MAC); the kernel's three-product form "
                              "executes 6 integer operations per complex MAC, so achieved/peak can reach 4/3; "
                              "hw_frac compares the executed operations with the peak",
                      "hw_ops_per_launch": hw_ops, "hw_tops": round(hw_tops, 3), "hw_frac": round(hw_tops / peak, 4),
                      "kernel": KERNEL_NAME, "avg_launch_ms": round(avg_kernel_ms, 4),
                      "algorithmic_bytes": in_bytes + out_bytes,
-                     "hbm_frac": round((in_bytes + out_bytes) / (avg_kernel_ms * 1e-3) / 1e9 /
-                                       (measured_peaks_file() or {}).get("hbm_gbs", 6699.8), 4)},
-        "peaks_tops": {"imma_s8": round(imma / 1e12, 2), "dp4a": round(dp4a / 1e12, 2),
-                       "imma_plus_dp4a": round(combo / 1e12, 2),
-                       "cublaslt_int8_gemm_8192": round(int_mm / 1e12, 2)},
-        "e2e": {"value": round(e2e, 3), "unit": "TOPS", "h2d_bytes_per_step": in_bytes,
-                "d2h_bytes_per_step": out_bytes, "h2d_gbs_measured": round(h2d_gbs, 1)},
+                     "hbm_frac": round((in_bytes + out_bytes) / (avg_kernel_ms * 1e-3) / 1e9 / hbm, 4)},
+        "e2e": {"value": round((job_ops or world * ops) * args.e2e_steps / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TOPS",
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
+                "h2d_gbs_measured": round(h2d_gbs, 1),
+                "ms_per_step": round(e2e_ms / args.e2e_steps, 4)},
         "gpu_launches": int(launches),
         "clocks": clocks,
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu_rec,
+    }
+    c.close()
+    del x_dev, x_host, out_host
+    torch.cuda.empty_cache()
+    return rec, max_ms, ops
+
+
+def run_xengine(args, wl_key):
+    import ctypes
+
+    import torch
+
+    import paper_1503_06203_gb300 as xe
+    import synth
+    from paper_1503_06203_gb300._lib import lib
+
+    rank, world, local = _dist_setup()
+    torch.cuda.set_device(local)
+    xe.build()
+    L = lib()
+    base = getattr(synth, WORKLOADS[wl_key][0])
+    bands = None
+    if args.split == "bands":
+        frame = base  # one frame shared by every rank
+        bands = xe.band_range(rank, world, base.F)
+    else:
+        frame = rank_frame(base, rank)
+    stream = torch.cuda.current_stream()
+    peaks = measure_peaks(L, ctypes.c_void_p(stream.cuda_stream))
+    frame_ops = 4.0 * frame.N * (frame.N + 1) * frame.F * frame.T
+    job_ops = frame_ops if args.split == "bands" else world * frame_ops
+    rec, max_ms, _ = single_frame_record(args, wl_key, frame, peaks, rank, world, bands, local, job_ops=job_ops)
+    if args.split == "bands":  # strong scaling: the one frame's operations over the slowest rank's time
+        value = frame_ops * args.steps / (max_ms * 1e-3) / 1e12
+        parallelism = f"bands of one frame split over {world} ranks" if world > 1 else "single GPU"
+    else:
+        value = aggregate_tops(world, frame_ops, args.steps, max_ms)
+        parallelism = f"one frame per rank, dp{world}" if world > 1 else "single GPU"
+    rec["config"]["parallelism"] = parallelism
+    line = {
+        "metric": "Effective TOPS", "value": round(value, 3), "unit": "TOPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_step"],
+        "higher_is_better": True, "scaling": "strong" if args.split == "bands" else "weak", "vs_baseline": None,
+        "dtype": "s8 x s8 -> s32", "data": "synthetic (seeded generator, paper's shapes)",
+        "config": rec["config"], "roofline": rec["roofline"],
+        "peaks_tops": {"imma_s8": round(peaks["imma"] / 1e12, 2), "dp4a": round(peaks["dp4a"] / 1e12, 2),
+                       "imma_plus_dp4a": round(peaks["combo"] / 1e12, 2),
+                       "cublaslt_int8_gemm_8192": round(peaks["int_mm"] / 1e12, 2)},
+        "e2e": rec["e2e"], "gpu_launches": rec["gpu_launches"], "clocks": rec["clocks"],
+        "cpu_baseline": rec["cpu_baseline"],
         "paper_context": "5.6 effective TOPS on an AMD R9 280X at N=2048 (context only)",
     }
+    if wl_key == "pathfinder" and world == 1 and not args.no_extras:
+        # the other workloads of the hot path, each timed on its own after the headline's timed region
+        ln, ln_ms, ln_ops = single_frame_record(args, "large_n", synth.LARGE_N, peaks, cpu_bands=1)
+        ln["value"] = round(ln_ops * args.steps / (ln_ms * 1e-3) / 1e12, 3)
+        ln["e2e"]["note"] = ("bound by the device-to-host readout of the 1.07 GB packed triangle each step "
+                             "(16x the input)")
+        line["large_n"] = ln
+        line["batched"] = batched_record(args)
+        line["served"] = served_record(args)
+        line["lags_gates"] = lags_gates_record(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    c.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
 # ----------------------------------------------------------------------------- batched / served
-def run_batched(args):
-    """64 uneven frames: one launch per frame vs one batched (graph-replayed) launch per step."""
+def batched_record(args) -> dict:
+    """64 uneven frames: one launch per frame (back to back, no host waits) vs one batched
+    (graph-replayed) launch per step. Both modes run the same frames into the same handles."""
+    import numpy as np
     import torch
 
+    import oracle
     import paper_1503_06203_gb300 as xe
     import synth
-    xe.build()
     frames = synth.batched_frames()
     cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
-    xs = [torch.from_numpy(f.make()).cuda() for f in frames]
+    xs_host = [f.make() for f in frames]
+    xs = [torch.from_numpy(x).cuda() for x in xs_host]
     ops = sum(4.0 * f.N * (f.N + 1) * f.F * f.T for f in frames)
     stream = torch.cuda.current_stream()
 
@@ -475,6 +564,7 @@ def run_batched(args):
                 c.accumulate(x)
 
     res = {}
+    sampler = ClockSampler(0).start()
     for mode in (False, True):
         for _ in range(args.warmup):
             step(mode)
@@ -486,30 +576,53 @@ def run_batched(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
-        res["batched" if mode else "plain"] = {"ms_per_step": round(ms, 4), "frames_per_s": round(len(frames) / ms * 1e3, 2),
+        res["batched" if mode else "plain"] = {"ms_per_step": round(ms, 4),
+                                               "frames_per_s": round(len(frames) / ms * 1e3, 2),
                                                "effective_tops": round(ops / ms / 1e9, 3),
                                                "launches_per_step": 1 if mode else len(frames)}
-    line = {"metric": "Effective TOPS", "value": res["batched"]["effective_tops"], "unit": "TOPS", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "s8 x s8 -> s32",
-            "data": "synthetic (seeded generator, paper's shapes)",
+    clocks = sampler.stop()
+    # the batched result of the last step against the oracle: sampled entries of every frame
+    rng = np.random.default_rng(5)
+    for fr, c, x in zip(frames, cors, xs_host):
+        V = c.readout().cpu().numpy()
+        K = 16
+        f = rng.integers(0, fr.F, K)
+        i = rng.integers(0, fr.N, K)
+        j = rng.integers(0, fr.N, K)
+        i, j = np.minimum(i, j), np.maximum(i, j)
+        if not np.array_equal(V[f, xe.packed_index(fr.N, i, j)].astype(np.int64),
+                              oracle.entries(x, np.stack([f, i, j], 1))):
+            raise RuntimeError("batched: result differs from the oracle")
+    for c in cors:
+        c.close()
+    del xs
+    torch.cuda.empty_cache()
+    return {"metric": "Effective TOPS", "value": res["batched"]["effective_tops"], "unit": "TOPS",
+            "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "64 uneven frames (N 64..2048, F 1..64, T 512..8192, sigma 1.5..3.5) per step",
-                       "frames": len(frames), "effective_ops_per_step": ops},
+                       "frames": len(frames), "effective_ops_per_step": ops,
+                       "l2": "inputs (6.1 GB per step) larger than L2, no flush"},
             "batched": res["batched"], "plain": res["plain"],
-            "speedup_batched_over_plain": round(res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"], 3)}
-    print(json.dumps(line), flush=True)
+            "speedup_batched_over_plain": round(res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"], 3),
+            "clocks": clocks}
 
 
-def run_served(args):
-    """32 served streams with Poisson arrivals: continuous batching vs one frame per launch."""
+def served_specs():
     import numpy as np
+
+    from paper_1503_06203_gb300 import serve
+    rng = np.random.default_rng(1004)
+    return [serve.StreamSpec(int(rng.choice([256, 1024, 2048])), int(rng.choice([16, 64, 256]))) for _ in range(32)]
+
+
+def served_record(args) -> dict:
+    """32 served streams with Poisson arrivals at each rate: continuous batching vs one frame per launch,
+    the same arrivals (seeded by the rate) for both."""
     import torch
 
-    import paper_1503_06203_gb300 as xe
     import synth
     from paper_1503_06203_gb300 import serve
-    xe.build()
-    rng = np.random.default_rng(1004)
-    specs = [serve.StreamSpec(int(rng.choice([256, 1024, 2048])), int(rng.choice([16, 64, 256]))) for _ in range(32)]
+    specs = served_specs()
     t_min, t_max = 1024, 8192
     pool_bytes = max(s.N * s.F for s in specs) * t_max
     pool = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory()
@@ -517,41 +630,48 @@ def run_served(args):
     budget = 24 << 30
     srv = serve.Server(specs, t_max, pool, budget_bytes=budget, readout_every=16)
     sweeps = []
+    sampler = ClockSampler(0).start()
     for rate in (float(r) for r in args.rates.split(",")):
-        # seeded by the rate itself, so a rate gets the same arrivals in any sweep
-        arr = serve.poisson_arrivals(rate, args.served_frames, len(specs), t_min, t_max, pool_bytes, specs,
+        count = args.served_frames or int(min(160, max(48, 6 * rate)))
+        arr = serve.poisson_arrivals(rate, count, len(specs), t_min, t_max, pool_bytes, specs,
                                      1004000 + int(round(10 * rate)))
-        out = {"rate_hz": rate}
+        out = {"rate_hz": rate, "frames": count}
         for mode in ("served", "plain"):
             srv.reset()
             st = srv.run_served(arr) if mode == "served" else srv.run_plain(arr)
             out[mode] = st.summary()
+        out["served_beats_plain"] = {
+            "frames_per_s": out["served"]["frames_per_s"] >= out["plain"]["frames_per_s"],
+            "p99": out["served"]["p99_ms"] <= out["plain"]["p99_ms"]}
         sweeps.append(out)
-    best = max(sweeps, key=lambda d: d["served"]["frames_per_s"])
+    clocks = sampler.stop()
     acc_gb = sum(s.F * s.N * (s.N + 1) * 4 for s in specs) / 1e9
-    line = {"metric": "served frames/s and p50/p99 frame latency (continuous batching vs one frame per launch)",
-            "value": best["served"]["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "s8 x s8 -> s32", "data": "synthetic (seeded generator, paper's shapes)",
+    srv.close()
+    del pool
+    torch.cuda.empty_cache()
+    return {"metric": "served frames/s and p50/p99 frame latency (continuous batching vs one frame per launch)",
+            "unit": "frames/s",
             "config": {"workload": "32 streams, N in {256,1024,2048}, F in {16,64,256} per stream, T 1024..8192 "
                                    "per frame, Poisson arrivals, readout every 16 frames",
                        "streams": [[s.N, s.F] for s in specs], "resident_accumulators_gb": round(acc_gb, 2),
-                       "input_budget_gb": budget / 2 ** 30, "frames_per_rate": args.served_frames},
-            "sweep": sweeps}
-    print(json.dumps(line), flush=True)
+                       "input_budget_gb": budget / 2 ** 30},
+            "sweep": sweeps, "clocks": clocks}
 
 
-def run_lags_gates(args):
+def lags_gates_record(args) -> dict:
     """Sec. IV extensions on the Pathfinder frame: lag-shift bandwidth, gated vs plain correlation."""
     import numpy as np
     import torch
 
+    import oracle
     import paper_1503_06203_gb300 as xe
     import synth
-    xe.build()
     fr = synth.PATHFINDER
     N, F, T = fr.N, fr.F, fr.T
-    x = torch.from_numpy(fr.make()).cuda()
-    lags = torch.from_numpy(np.random.default_rng(7).integers(-64, 64, N).astype(np.int32)).cuda()
+    x_np = fr.make()
+    x = torch.from_numpy(x_np).cuda()
+    lags_np = np.random.default_rng(7).integers(-64, 64, N).astype(np.int32)
+    lags = torch.from_numpy(lags_np).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()
 
@@ -568,6 +688,9 @@ def run_lags_gates(args):
         return a.elapsed_time(b) / reps
 
     ms_shift = timed(lambda: xe.shift_lags(x, lags, out=y), 20)
+    # two bands of the shifted frame against the oracle's shift
+    if not np.array_equal(y[:, :2, :].cpu().numpy(), oracle.shift_lags(np.ascontiguousarray(x_np[:, :2, :]), lags_np)):
+        raise RuntimeError("lag shift differs from the oracle")
     gbs = 2.0 * N * F * T / ms_shift / 1e6
     hbm = (measured_peaks_file() or {}).get("hbm_gbs", 6699.8)
     G, period = 8, 1024
@@ -586,18 +709,48 @@ def run_lags_gates(args):
     ms_gated = timed(gated_step, 10)
     ms_plain = timed(plain_step, 10)
     ops = 4.0 * N * (N + 1) * F * T
-    line = {"metric": "lag shift GB/s and gated-correlation effective TOPS", "value": round(ops / ms_gated / 1e9, 3),
-            "unit": "TOPS", "n_gpus": 1, "higher_is_better": True, "dtype": "s8 x s8 -> s32",
-            "data": "synthetic (seeded generator, paper's shapes)",
-            "config": {"workload": "Pathfinder frame N=256 F=256 T=16384; lags uniform in [-64, 64); "
+    for c in gates + [plain]:
+        c.close()
+    del x, y
+    torch.cuda.empty_cache()
+    return {"config": {"workload": "Pathfinder frame N=256 F=256 T=16384; lags uniform in [-64, 64); "
                                    f"{G} gates of a {period}-sample period"},
-            "lag_shift": {"ms": round(ms_shift, 4), "gbs": round(gbs, 1), "hbm_peak_gbs": hbm,
-                          "frac": round(gbs / hbm, 4), "bound": "hbm",
-                          "algorithmic_bytes": 2 * N * F * T},
+            "lag_shift": {"kernel": "shift_lags_stream_kernel", "ms": round(ms_shift, 4), "gbs": round(gbs, 1),
+                          "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                                       "frac": round(gbs / hbm, 4), "algorithmic_bytes": 2 * N * F * T}},
             "gated": {"ms": round(ms_gated, 4), "effective_tops": round(ops / ms_gated / 1e9, 3), "gates": G,
                       "segments": T // (period // G)},
             "plain": {"ms": round(ms_plain, 4), "effective_tops": round(ops / ms_plain / 1e9, 3)}}
+
+
+def _standalone(args, metric, unit, rec):
+    import paper_1503_06203_gb300 as xe  # noqa: F401
+    line = {"metric": metric, "unit": unit, "n_gpus": 1, "higher_is_better": True, "dtype": "s8 x s8 -> s32",
+            "data": "synthetic (seeded generator, paper's shapes)", **rec}
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args):
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    rec = batched_record(args)
+    _standalone(args, rec.pop("metric"), rec.pop("unit"), rec)
+
+
+def run_served(args):
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    rec = served_record(args)
+    rec["value"] = max(d["served"]["frames_per_s"] for d in rec["sweep"])
+    _standalone(args, rec.pop("metric"), rec.pop("unit"), rec)
+
+
+def run_lags_gates(args):
+    import paper_1503_06203_gb300 as xe
+    xe.build()
+    rec = lags_gates_record(args)
+    rec["value"] = rec["gated"]["effective_tops"]
+    _standalone(args, "lag shift GB/s and gated-correlation effective TOPS", "TOPS", rec)
 
 
 def main():

@@ -65,20 +65,44 @@ enum {
 
 /*
  * corr_create -- make a handle for frames of N elements, F bands and T time
- * samples (1 <= N <= CORR_MAX_N, F >= 1, T >= 1, F*B(N)*2 int32 accumulators
- * addressable). The handle allocates its own device accumulators on the
- * current CUDA device and starts in the reset (all-zero) state.
+ * samples (the problem of Sec. II.A: N inputs, each band's N x N matrix
+ * accumulated over time samples; 1 <= N <= CORR_MAX_N, F >= 1, T >= 1,
+ * F*B(N)*2 int32 accumulators addressable). The handle allocates its own
+ * device accumulators on the current CUDA device and starts in the reset
+ * (all-zero) state; they stay resident until corr_destroy.
  * Returns NULL on error; corr_last_error() says why.
  */
 corr_handle_t* corr_create(int32_t N, int32_t F, int32_t T);
 
 /*
- * corr_create_ex -- as corr_create, but the accumulators live in a caller-
- * owned device buffer acc_dev of F*N(N+1)/2*2 int32 (e.g. a torch tensor),
- * 16-byte aligned. The caller keeps it alive until corr_destroy. Its
- * contents on entry are ignored: the handle starts in the reset state.
+ * corr_create_ex -- as corr_create (Sec. II.A; library lifecycle), but the
+ * accumulators live in a caller-owned device buffer acc_dev of
+ * F*N(N+1)/2*2 int32 (e.g. a torch tensor), 16-byte aligned. The caller
+ * keeps it alive until corr_destroy. Its contents on entry are ignored: the
+ * handle starts in the reset state.
  */
 corr_handle_t* corr_create_ex(int32_t N, int32_t F, int32_t T, int32_t* acc_dev);
+
+/*
+ * corr_create_bands -- a handle for the bands [f0, f1) of frames that hold
+ * F_in bands (Sec. I and Sec. IV: frequency bands are independent, so the
+ * bands of one frame can be split across GPUs with no exchange; each GPU
+ * holds a handle for its own range). 0 <= f0 < f1 <= F_in. Every call that
+ * takes a frame (corr_accumulate, corr_accumulate_host, the batched and
+ * gated calls) then takes the whole frame uint8 x[T][F_in][N] and reads only
+ * the handle's bands; corr_readout gives int32 V[f1 - f0][B][2], band f0
+ * first. The visibilities of the ranges of a partition of [0, F_in),
+ * concatenated in band order, equal those of one handle over all F_in bands.
+ * Otherwise as corr_create (the handle's F is f1 - f0). NULL on error.
+ */
+corr_handle_t* corr_create_bands(int32_t N, int32_t F_in, int32_t f0, int32_t f1, int32_t T);
+
+/*
+ * corr_bands -- the handle's input band count and band range [f0, f1)
+ * (F_in = f1 - f0 = F and f0 = 0 for handles from corr_create). Any pointer
+ * may be NULL. CORR_EINVAL for a NULL handle.
+ */
+int corr_bands(const corr_handle_t* h, int32_t* F_in, int32_t* f0, int32_t* f1);
 
 /*
  * corr_accumulate -- add one frame to the handle's accumulators
@@ -160,12 +184,24 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
  *     library default (1 unless the XE_PRODUCT=mma environment variable is
  *     set). Batched and gated launches treat 2 as 1.
  *   CORR_OPT_SPLIT: 0 = automatic time split, k >= 1 = cut the time axis into
- *     k ranges (atomic adds when k > 1).
- * A batched launch takes its product path from its first handle.
- * Returns CORR_OK or CORR_EINVAL.
+ *     k ranges (atomic adds when k > 1). Changing it rebuilds the handle's
+ *     schedule, so the handle must be idle (its last call finished, e.g.
+ *     after corr_synchronize): otherwise CORR_EBUSY and nothing changes.
+ *   CORR_OPT_MMA_STEPS: for product paths 1 and 2, how many of every 8
+ *     k-steps of 32 samples (two 128-sample chunks) run on the tensor cores,
+ *     the rest on dp4a: 8 = tensor cores only, 7 (chunks alternate 128/0 and
+ *     96/32), 6 (the default, 96/32 in every chunk), 5 (alternate 64/64 and
+ *     96/32), 4 (64/64). The two pipes run side by side on this GPU, so the
+ *     share sets how the work is balanced between them. Single-frame calls
+ *     (corr_accumulate, corr_accumulate_host) on product path 1 take every
+ *     share; batched and gated calls and product path 2 take 8 or 6 (other
+ *     values run as 6).
+ * A batched launch takes its product path and share from its first handle.
+ * Returns CORR_OK, CORR_EINVAL or CORR_EBUSY.
  */
 #define CORR_OPT_PRODUCT 1
 #define CORR_OPT_SPLIT 2
+#define CORR_OPT_MMA_STEPS 3
 int corr_set_option(corr_handle_t* h, int option, int64_t value);
 int64_t corr_get_option(const corr_handle_t* h, int option);
 
@@ -183,10 +219,13 @@ int64_t corr_get_option(const corr_handle_t* h, int option);
 int corr_accumulate_gated(corr_handle_t* const* gates, int G, const uint8_t* packed_dev, int32_t T, int32_t period,
                           int32_t phase, void* stream);
 
-/* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit). */
+/* corr_synchronize -- wait (host) for the handle's last call, at most timeout_ms (<0: no limit);
+ * library lifecycle, no counterpart in the paper. */
 int corr_synchronize(corr_handle_t* h, int64_t timeout_ms);
 
-/* corr_status -- CORR_OK or the handle's sticky error (CUDA failure or device fault report). */
+/* corr_status -- CORR_OK or the handle's sticky error (CUDA failure or device fault report); library
+ * lifecycle, no counterpart in the paper. Reads the device fault word with a copy ordered after the
+ * handle's last call (it waits for that call to finish, but not for other work on other streams). */
 int corr_status(corr_handle_t* h);
 
 /* corr_samples -- samples accumulated since the last reset. */
@@ -201,7 +240,8 @@ int corr_dims(const corr_handle_t* h, int32_t* N, int32_t* F, int32_t* T);
 /* corr_last_error -- message for the calling thread's last failed call ("" if none). */
 const char* corr_last_error(void);
 
-/* corr_destroy -- wait for the handle's work, free what it owns. NULL is a no-op. */
+/* corr_destroy -- wait for the handle's work, free what it owns. NULL is a no-op. Library lifecycle,
+ * no counterpart in the paper. */
 void corr_destroy(corr_handle_t* h);
 
 /*
@@ -236,11 +276,11 @@ double corr_effective_ops(int32_t N, int32_t F, int32_t T);
 
 /*
  * corr_correlate_noalloc -- correlate one frame without allocating anything.
- * (The paper has no counterpart: this is a service for callers that cannot
- * allocate device memory when they correlate: code running while a stream
- * is captured into a CUDA graph, where cudaMalloc/cudaFree are not allowed;
- * applications whose device memory belongs to their own pool allocator; and
- * real-time hosts that reserve all memory up front.)
+ * (The paper has no counterpart.) It serves callers that cannot allocate
+ * device memory at the moment they correlate: applications whose device
+ * memory belongs to their own pool allocator, which must not have memory
+ * taken behind its back, and real-time hosts that reserve every byte before
+ * they start and forbid allocation on their processing path.
  *
  * packed_dev: device frame uint8 x[T][F][N] (layout above); N must be a
  *   multiple of 16 and the pointer 16-byte aligned (no staging copy here).
@@ -255,11 +295,14 @@ double corr_effective_ops(int32_t N, int32_t F, int32_t T);
  * without launching anything. The call uses no cudaMalloc, cudaFree or other
  * allocating routine; on success it touches no allocator at all (a failure
  * records its message for corr_last_error). Asynchronous on `stream`.
- * The first call on each device looks up the array's device address and
- * sets the kernel's shared-memory limit; make that first call before any
- * stream capture. All calls share the one array and each call rewrites it,
- * so calls that can overlap on the GPU (different streams, no ordering
- * between them) race and must not be issued; calls on one stream are safe.
+ * The first call on each device, with that device current, looks up the
+ * array's device address and sets the kernel's shared-memory limit; make
+ * that first call before any stream capture. The address is kept for the
+ * life of the process, so cudaDeviceReset must not be called while the
+ * library is in use. All calls share the one array and each call rewrites
+ * it (the fault word is cleared at the start of every call), so calls that
+ * can overlap on the GPU (different streams, no ordering between them) race
+ * and must not be issued; calls on one stream are safe.
  */
 int corr_correlate_noalloc(const uint8_t* packed_dev, int32_t N, int32_t F, int32_t T, int32_t* vis_dev,
                            int32_t* status_dev, void* stream);

@@ -11,10 +11,12 @@ import ctypes
 import numpy as np
 
 from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_MAX_SAMPLES, CORR_OK,
-                   CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
+                   CORR_OPT_MMA_STEPS, CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
-           "plan_schedule", "correlate_noalloc", "selftest_wait_timeout", "shift_lags", "accumulate_gated", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N", "build", "last_error"]
+           "plan_schedule", "correlate_noalloc", "selftest_wait_timeout", "shift_lags", "accumulate_gated",
+           "band_range", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "CORR_OPT_MMA_STEPS", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N",
+           "build", "last_error"]
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +63,19 @@ def plan_schedule(N: int, F: int, T: int, ctas: int):
     return items, grid.value
 
 
+def band_range(rank: int, world: int, F: int):
+    """Bands [f0, f1) of rank `rank` of `world` when F independent bands are split across GPUs (Sec. I, Sec. IV).
+
+    Contiguous ranges in rank order, sizes differing by at most one; every band
+    belongs to exactly one rank. A rank beyond F gets an empty range (f0 == f1).
+    """
+    if not (0 <= rank < world) or F < 1:
+        raise ValueError(f"bad partition: rank {rank} of {world}, F={F}")
+    base, extra = divmod(F, world)
+    f0 = rank * base + min(rank, extra)
+    return f0, f0 + base + (1 if rank < extra else 0)
+
+
 def _stream_ptr(stream):
     import torch
     if stream is None:
@@ -69,12 +84,24 @@ def _stream_ptr(stream):
 
 
 class Correlator:
-    """A handle: resident int32 accumulators for frames of N elements, F bands, T samples."""
+    """A handle: resident int32 accumulators for frames of N elements, F bands, T samples.
 
-    def __init__(self, N: int, F: int, T: int, acc=None):
+    With bands=(f0, f1) the handle correlates only bands [f0, f1) of frames that
+    hold F bands (corr_create_bands): frames passed to it are [T][F][N], its
+    visibilities are [f1 - f0][N(N+1)/2][2], and self.F is f1 - f0 (self.F_in = F).
+    """
+
+    def __init__(self, N: int, F: int, T: int, acc=None, bands=None):
         L = lib()
         self._acc = acc  # keep a caller-owned tensor alive
-        if acc is None:
+        self.F_in, self.f0 = F, 0
+        if bands is not None:
+            if acc is not None:
+                raise ValueError("a band-range handle owns its accumulators")
+            f0, f1 = bands
+            h = L.corr_create_bands(N, F, f0, f1, T)
+            self.F_in, self.f0, F = F, f0, f1 - f0
+        elif acc is None:
             h = L.corr_create(N, F, T)
         else:
             import torch
@@ -106,8 +133,8 @@ class Correlator:
 
     # -- calls --
     def _check_frame(self, x):
-        if tuple(x.shape) != (self.T, self.F, self.N):
-            raise ValueError(f"frame shape {tuple(x.shape)} != (T, F, N) = {(self.T, self.F, self.N)}")
+        if tuple(x.shape) != (self.T, self.F_in, self.N):
+            raise ValueError(f"frame shape {tuple(x.shape)} != (T, F, N) = {(self.T, self.F_in, self.N)}")
 
     def accumulate(self, x, stream=None):
         """Add a device frame (torch uint8 [T][F][N], contiguous) to the accumulators."""
@@ -153,7 +180,7 @@ class Correlator:
         return int(lib().corr_samples(self._h))
 
     def set_option(self, option: int, value: int):
-        """Launch knobs (results never depend on them): CORR_OPT_PRODUCT, CORR_OPT_SPLIT."""
+        """Launch knobs (results never depend on them): CORR_OPT_PRODUCT, CORR_OPT_SPLIT, CORR_OPT_MMA_STEPS."""
         check(lib().corr_set_option(self._h, option, int(value)))
 
     def get_option(self, option: int) -> int:
@@ -192,7 +219,7 @@ def accumulate_gated(gates, x, period: int, phase: int = 0, stream=None):
     G = len(gates)
     T, F, N = x.shape
     for c in gates:
-        if (c.N, c.F) != (N, F):
+        if (c.N, c.F_in) != (N, F):
             raise ValueError("gate correlators must match the frame's N and F")
     hs = (ctypes.c_void_p * G)(*[c._h.value for c in gates])
     check(lib().corr_accumulate_gated(hs, G, ctypes.c_void_p(x.data_ptr()), T, period, phase, _stream_ptr(stream)))
@@ -201,9 +228,10 @@ def accumulate_gated(gates, x, period: int, phase: int = 0, stream=None):
 def correlate_noalloc(x, out, status=None, stream=None):
     """One frame into `out` (int32 [F][N(N+1)/2][2], overwritten) with no allocation by the library.
 
-    For callers that cannot allocate device memory at call time (graph capture,
-    a foreign pool allocator, real-time hosts): the work list lives in a fixed
-    1 MiB array inside the library. `x` is a contiguous CUDA uint8 [T][F][N]
+    For callers that cannot allocate device memory at call time (an
+    application's own pool allocator owns the memory, or a real-time host
+    forbids allocation on its processing path): the work list lives in a
+    fixed 1 MiB array inside the library. `x` is a contiguous CUDA uint8 [T][F][N]
     tensor with N a multiple of 16; `status`, if given, is a CUDA int32 tensor
     that receives the kernel's fault word (0 = no fault). Calls that may overlap
     on the GPU race on the shared array; keep them on one stream.
@@ -230,7 +258,7 @@ def accumulate_batch(correlators, inputs, stream=None):
     n = len(correlators)
     assert len(inputs) == n
     for c, x in zip(correlators, inputs):
-        if tuple(x.shape[1:]) != (c.F, c.N) or not x.is_contiguous():
+        if tuple(x.shape[1:]) != (c.F_in, c.N) or not x.is_contiguous():
             raise ValueError(f"frame shape {tuple(x.shape)} does not fit (T, F, N) with F={c.F}, N={c.N}")
     hs = (ctypes.c_void_p * n)(*[c._h.value for c in correlators])
     xs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in inputs])

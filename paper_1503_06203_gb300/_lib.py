@@ -17,6 +17,7 @@ CORR_EBUSY = -6
 CORR_MAX_N = 16384
 CORR_OPT_PRODUCT = 1
 CORR_OPT_SPLIT = 2
+CORR_OPT_MMA_STEPS = 3
 CORR_MAX_SAMPLES = 16777215
 
 # (name, restype, argtypes) for every symbol include/xengine.h declares
@@ -24,6 +25,8 @@ _vp, _i32, _i64, _int = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.
 SIGNATURES = [
     ("corr_create", _vp, [_i32, _i32, _i32]),
     ("corr_create_ex", _vp, [_i32, _i32, _i32, _vp]),
+    ("corr_create_bands", _vp, [_i32, _i32, _i32, _i32, _i32]),
+    ("corr_bands", _int, [_vp, _vp, _vp, _vp]),
     ("corr_accumulate", _int, [_vp, _vp, _vp]),
     ("corr_accumulate_host", _int, [_vp, _vp, _vp]),
     ("corr_readout", _int, [_vp, _vp, _int, _vp]),

@@ -2,8 +2,11 @@
 
 Knobs (results never depend on them; see corr_set_option in include/xengine.h):
 the product path (tensor cores + dp4a, tensor cores alone, or tensor cores +
-dp4a on offset-encoded operands with the Eq. 3 corrections) and the time
-split (automatic, or a fixed number of ranges). For a frame shape (N, F, T)
+dp4a on offset-encoded operands with the Eq. 3 corrections), the share of
+each pair of 128-sample chunks that runs on the tensor cores (8, 7, 6, 5 or 4
+of 8 k-steps of 32 samples, the rest on dp4a; each share is its own kernel
+instantiation, built in), and the time split (automatic, or a fixed number
+of ranges). For a frame shape (N, F, T)
 the tuner times every candidate with CUDA events on random frames and keeps
 the fastest in a JSON cache keyed by the GPU and the shape, so a shape is
 tuned once per GPU model. The library default (the first candidate) stays
@@ -15,10 +18,12 @@ from __future__ import annotations
 import json
 import os
 
-from . import CORR_OPT_PRODUCT, CORR_OPT_SPLIT, Correlator
+from . import CORR_OPT_MMA_STEPS, CORR_OPT_PRODUCT, CORR_OPT_SPLIT, Correlator
 
 CACHE_ENV = "XE_TUNE_CACHE"
-PRODUCTS = (1, 0, 2)   # tensor cores + dp4a, tensor cores alone, offset-encoded operands (Eq. 3)
+# (product path, tensor-core k-steps of 8): tensor cores + dp4a at every share (the library default, 6,
+# first), tensor cores alone, offset-encoded operands (Eq. 3)
+PATHS = ((1, 6), (1, 7), (1, 5), (1, 4), (0, 8), (2, 6))
 SPLITS = (0, 1, 2, 4)  # automatic, fixed
 MARGIN = 0.01          # relative speed-up a candidate needs over the default
 
@@ -38,8 +43,9 @@ def shape_key(N: int, F: int, T: int) -> str:
 
 
 def candidates(T: int):
+    """(product, mma_steps, split) in trial order; the library default first."""
     nch = -(-T // 128)
-    return [(p, s) for p in PRODUCTS for s in SPLITS if s <= nch]
+    return [(p, m, s) for p, m in PATHS for s in SPLITS if s <= nch]
 
 
 def load_cache(path: str | None = None) -> dict:
@@ -60,11 +66,17 @@ def save_cache(cache: dict, path: str | None = None):
     os.replace(tmp, path)
 
 
-def time_config(c: Correlator, x, product: int, split: int, reps: int) -> float:
-    """Median ms of one frame accumulate under (product, split)."""
-    import torch
+def set_knobs(c: Correlator, product: int, mma_steps: int, split: int):
     c.set_option(CORR_OPT_PRODUCT, product)
+    c.set_option(CORR_OPT_MMA_STEPS, mma_steps)
     c.set_option(CORR_OPT_SPLIT, split)
+
+
+def time_config(c: Correlator, x, product: int, mma_steps: int, split: int, reps: int) -> float:
+    """Median ms of one frame accumulate under (product, mma_steps, split)."""
+    import torch
+    torch.cuda.synchronize()  # the split option needs the handle idle
+    set_knobs(c, product, mma_steps, split)
     for _ in range(2):
         c.reset()
         c.accumulate(x)
@@ -98,10 +110,12 @@ def tune(N: int, F: int, T: int, reps: int = 5, path: str | None = None, force: 
     x = torch.randint(0, 256, (T, F, N), dtype=torch.uint8, device="cuda")
     trials = []
     with Correlator(N, F, T) as c:
-        for product, split in candidates(T):
-            trials.append({"product": product, "split": split, "ms": round(time_config(c, x, product, split, reps), 4)})
+        for product, mma_steps, split in candidates(T):
+            ms = time_config(c, x, product, mma_steps, split, reps)
+            trials.append({"product": product, "mma_steps": mma_steps, "split": split, "ms": round(ms, 4)})
     best = pick(trials)
-    entry = {"product": best["product"], "split": best["split"], "ms": best["ms"], "trials": trials}
+    entry = {"product": best["product"], "mma_steps": best["mma_steps"], "split": best["split"], "ms": best["ms"],
+             "trials": trials}
     cache = load_cache(path)  # re-read: another process may have written meanwhile
     cache.setdefault(g, {})[k] = entry
     save_cache(cache, path)
@@ -115,6 +129,5 @@ def apply(c: Correlator, path: str | None = None, tune_if_missing: bool = True) 
     if entry is None and tune_if_missing:
         entry = tune(c.N, c.F, c.T, path=path)
     if entry is not None:
-        c.set_option(CORR_OPT_PRODUCT, entry["product"])
-        c.set_option(CORR_OPT_SPLIT, entry["split"])
+        set_knobs(c, entry["product"], entry.get("mma_steps", 6), entry["split"])
     return entry

@@ -54,6 +54,14 @@ struct FrameDesc {  // (aligned as its CUtensorMap)
   int32_t* vis;      // [F][B][2] accumulators of the frame's handle
   int32_t t0;        // samples before t0 count as zero (gated segments); 0 for whole frames
   int32_t atomic;    // 1: add atomically (several segments feed the same accumulators)
+  // for the device-side work list of batched launches (xe_batch.cuh)
+  int32_t F;         // bands
+  int32_t nb;        // tile rows: ceil(N / kTile)
+  int32_t per;       // chunks per time range of the frame's items
+  // gated launches with gate windows by arithmetic (kGateArith): this
+  // descriptor is gate `gate` of G; sample t is in it when
+  // floor(((t + phase) mod period) * G / period) == gate (period >= kTC)
+  int32_t period, phase, G, gate;
 };
 
 struct CorrArgs {
@@ -69,7 +77,7 @@ struct CorrArgs {
   int64_t B;            // N(N+1)/2
   int32_t* vis;         // [F][B][2] accumulators
   int32_t fresh;        // 1: accumulators hold no integration yet (whole tiles store)
-  int32_t hybrid;       // 0: tensor cores only; 1: the last 32 of each chunk's 128 samples on dp4a
+  int32_t hybrid;       // split of each chunk's 128 samples between tensor cores and dp4a (kSplit*)
   int32_t* err;         // device error word
 };
 
@@ -80,7 +88,8 @@ struct CorrArgs {
 struct ChunkMeta {
   int32_t f;        // band
   int32_t bij;      // bi | bj << 16
-  int32_t lo, hi;   // valid rows of the chunk: [lo, hi)
+  int32_t lo, hi;   // valid rows of the chunk: [lo, hi) and [lo2, hi2)
+  int32_t lo2, hi2;
   int32_t flags;    // kMetaValid | kMetaEnd | write mode << 4 (kMetaEnd unset while a gated group holds)
   int32_t N;
   int64_t B;
@@ -129,14 +138,16 @@ __device__ __forceinline__ uint32_t plane_off(int e, int chunk) {
 // has a row-side factor Xr, Xi or Xr + Xi).
 template <bool kMasked, bool kEnc>
 __device__ __forceinline__ void unpack_unit(const uint8_t* box, uint32_t pl0, uint32_t pl1, uint32_t pl2,
-                                            bool side_b, int eg, int tg, int p, int lo, int hi) {
+                                            bool side_b, int eg, int tg, int p, int lo, int hi, int lo2 = 0,
+                                            int hi2 = 0) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(box);
   uint32_t r[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     const int t = 16 * tg + (k ^ p);
     r[k] = w[t * (kTile / 4) + eg];
-    if (kMasked) r[k] = (t >= lo && t < hi) ? r[k] : (kEnc ? 0u : 0x88888888u);  // rows outside [lo, hi): no products
+    // rows outside [lo, hi) and [lo2, hi2): no products
+    if (kMasked) r[k] = ((t >= lo && t < hi) || (t >= lo2 && t < hi2)) ? r[k] : (kEnc ? 0u : 0x88888888u);
   }
   const int s = eg & 1;
   const uint32_t selA = p ? 0x1504u : 0x5140u;  // interleave two rows, bytes 0-1
@@ -345,10 +356,47 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // four of them share each SM sub-partition. Warps 16-19 (warpgroup 4):
 // unpack; lane 0 of warp 16 also issues the TMA loads. One CTA per SM.
 
+// ---- gate arithmetic (kGateArith launches) --------------------------------------
+// Gate g of G holds the positions [a, b) of a period P, a = ceil(g P / G),
+// b = ceil((g + 1) P / G): floor(pos G / P) == g exactly there. Sample t has
+// position (t + phase) mod P. Chunks are kTC samples; P >= kTC, so a chunk's
+// positions wrap at most once and the gate meets a chunk in at most two runs.
+
+// The first sample >= s whose position lies in [a, b) (a < b <= P).
+__device__ __forceinline__ int64_t gate_next_sample(int64_t s, int32_t P, int32_t phase, int32_t a, int32_t b) {
+  const int32_t pos = static_cast<int32_t>((s + phase) % P);
+  if (pos >= a && pos < b) return s;
+  return s + (pos < a ? a - pos : P - pos + a);
+}
+
+// The first chunk >= c holding a sample t < T of the gate; nch if none.
+__device__ __forceinline__ int32_t gate_chunk(int32_t c, int32_t nch, int32_t T, int32_t P, int32_t phase, int32_t a,
+                                              int32_t b) {
+  if (c >= nch || a >= b) return nch;
+  const int64_t s = gate_next_sample(static_cast<int64_t>(c) * kTC, P, phase, a, b);
+  return s >= T ? nch : static_cast<int32_t>(s / kTC);
+}
+
+// The gate's rows of chunk c (relative to its first sample), as two windows
+// [lo, hi) and [lo2, hi2): the run before the chunk's positions wrap past P
+// and the run after it; both clipped to the frame's T samples.
+__device__ __forceinline__ void gate_windows(int32_t c, int32_t T, int32_t P, int32_t phase, int32_t a, int32_t b,
+                                             ChunkMeta& m) {
+  const int64_t s0 = static_cast<int64_t>(c) * kTC;
+  const int32_t p0 = static_cast<int32_t>((s0 + phase) % P);
+  const int32_t tmax = static_cast<int32_t>(min(static_cast<int64_t>(kTC), static_cast<int64_t>(T) - s0));
+  m.lo = max(0, a - p0);
+  m.hi = min(tmax, b - p0);
+  m.lo2 = max(0, a - p0 + P);
+  m.hi2 = min(tmax, b - p0 + P);
+}
+
 // Walks (item, chunk) pairs of this CTA in order. T and nch are the current
 // item's frame's (from its descriptor in a batch, else from args); the writer
-// reads the rest when it needs it.
-template <bool kFrames, bool kHold>
+// reads the rest when it needs it. kArith: the item is one (band, tile, gate)
+// over the frame, and its chunks are those that hold samples of the gate
+// (the current one c, the next one cn).
+template <bool kFrames, bool kHold, bool kArith = false>
 struct Walk {
   int item, c, f, bi, bj, c1, frame, T, nch, T0;
   const int4* items;
@@ -359,8 +407,10 @@ struct Walk {
   int mode, hold, fN, fresh, atomic;
   int64_t fB;
   int32_t* fvis;
+  // kArith: the gate of the current descriptor, and the item's next chunk
+  int gP, gphase, ga, gb, cn;
   __device__ __forceinline__ void load() {
-    if (item < nitems) {
+    for (; item < nitems; item += stride) {
       const int4 w = items[item];
       bi = w.y & 0xFFFF;
       c = w.z;
@@ -379,15 +429,28 @@ struct Walk {
           fvis = frames[fr].vis;
           fresh = frames[fr].fresh;
           atomic = frames[fr].atomic;
+          if (kArith) {
+            gP = frames[fr].period;
+            gphase = frames[fr].phase;
+            const int64_t G = frames[fr].G, g = frames[fr].gate;
+            ga = static_cast<int>((g * gP + G - 1) / G);
+            gb = static_cast<int>(((g + 1) * gP + G - 1) / G);
+          }
         }
         hold = kHold && w.y < 0;
         // a gated group covers all of its gate's samples in the frame, like a whole tile
-        const bool whole = kHold || (w.z == 0 && w.w == nch);
+        const bool whole = kHold || kArith || (w.z == 0 && w.w == nch);
         mode = atomic ? 2 : (whole ? (fresh ? 0 : 1) : 2);
+        if (kArith) {
+          c = gate_chunk(c, c1, T, gP, gphase, ga, gb);
+          if (c >= c1) continue;  // the gate has no samples here: nothing to do or write
+          cn = gate_chunk(c + 1, c1, T, gP, gphase, ga, gb);
+        }
       } else {
         bj = w.y >> 16;
         f = w.x;
       }
+      return;
     }
   }
   __device__ __forceinline__ void start(const CorrArgs& a) {
@@ -403,11 +466,20 @@ struct Walk {
     load();
   }
   __device__ __forceinline__ bool valid() const { return item < nitems; }
+  // the current chunk is the item's last
+  __device__ __forceinline__ bool last() const { return kArith ? cn >= c1 : c + 1 == c1; }
   __device__ __forceinline__ void next() {
-    if (++c == c1) {
-      item += stride;
-      load();
+    if (kArith) {
+      if (cn < c1) {
+        c = cn;
+        cn = gate_chunk(c + 1, c1, T, gP, gphase, ga, gb);
+        return;
+      }
+    } else if (++c != c1) {
+      return;
     }
+    item += stride;
+    load();
   }
   __device__ __forceinline__ const CUtensorMap* map(const CUtensorMap* single) const {
     return kFrames ? &frames[frame].map : single;
@@ -423,11 +495,51 @@ struct Walk {
 // (2 bits per warp: piece row, piece column, selection)
 constexpr uint32_t kDiagR = 0xfa9050u, kDiagC = 0xfaedd8u, kDiagSel = 0xff990000u;
 
+// Split of a chunk's 128 samples between the tensor cores (k-steps of 32)
+// and dp4a (the rest), chosen per launch: the same split for every chunk, or
+// two splits alternating between consecutive chunks of a CTA, which gives the
+// finer average shares in between. Every split gives the same exact sums.
+// Tensor-core k-steps per pair of chunks:
+enum : int {
+  kSplitMma = 0,   // 8 of 8: tensor cores only
+  kSplit6 = 1,     // 6 of 8 (96 / 32 per chunk)
+  kSplit7 = 2,     // 7 of 8 (alternating 128 / 0 and 96 / 32)
+  kSplit5 = 3,     // 5 of 8 (alternating 64 / 64 and 96 / 32)
+  kSplit4 = 4      // 4 of 8 (64 / 64 per chunk)
+};
+
+// Tensor-core k-steps of a chunk under split `hybrid`; odd = the CTA's chunk count is odd.
+__device__ __forceinline__ int mma_ksteps(int hybrid, int odd) {
+  switch (hybrid) {
+    case kSplit6: return 3;
+    case kSplit7: return odd ? 4 : 3;
+    case kSplit5: return odd ? 2 : 3;
+    case kSplit4: return 2;
+    default: return 4;
+  }
+}
+
+template <int sel, bool kEnc>
+__device__ __forceinline__ void chunk_split(int mk, uint32_t a_base, uint32_t b01, uint32_t b2, int pr, int pc,
+                                            int lane, int32_t (&acc)[3][2][4]) {
+  if (mk == 3)
+    chunk_hybrid<sel, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+  else if (mk == 2)
+    chunk_hybrid<sel, 2, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+  else
+    chunk_mma<sel, kEnc>(a_base, b01, b2, pr, pc, lane, kTC / 32, acc);
+}
+
 // One product warp's share of one chunk in plane buffer `buf`; nvalid = valid
-// rows of the chunk. Returns the warp's piece (pr, pc) and selection.
-template <bool kEnc>
+// rows of the chunk; it = the CTA's chunk count. kSplitT < 0: the split is
+// args.hybrid, kSplitMma or kSplit6, chosen at run time; else the split is
+// kSplitT, fixed at compile time (one instantiation per split keeps the hot
+// loop to two code paths and within the register budget). Returns the warp's
+// piece (pr, pc) and selection.
+template <bool kEnc, int kSplitT>
 __device__ __forceinline__ void product_chunk(CorrSmem& sm, int buf, int warp, int lane, bool diag, int nvalid,
-                                              int hybrid, int& pr, int& pc, int& sel, int32_t (&acc)[3][2][4]) {
+                                              int hybrid, uint32_t it, int& pr, int& pc, int& sel,
+                                              int32_t (&acc)[3][2][4]) {
   pr = diag ? static_cast<int>((kDiagR >> (2 * warp)) & 3) : warp >> 2;
   pc = diag ? static_cast<int>((kDiagC >> (2 * warp)) & 3) : warp & 3;
   sel = diag ? static_cast<int>((kDiagSel >> (2 * warp)) & 3) : kSelAll;
@@ -436,13 +548,15 @@ __device__ __forceinline__ void product_chunk(CorrSmem& sm, int buf, int warp, i
   const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
   const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
   const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
-  if (hybrid == 1 && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
+  const int split = kSplitT < 0 ? (hybrid == kSplitMma ? kSplitMma : kSplit6) : kSplitT;
+  if (split != kSplitMma && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
+    const int mk = mma_ksteps(split, static_cast<int>(it & 1));
     if (sel == kSelAll)
-      chunk_hybrid<kSelAll, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+      chunk_split<kSelAll, kEnc>(mk, a_base, b01, b2, pr, pc, lane, acc);
     else if (sel == kSelN0)
-      chunk_hybrid<kSelN0, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+      chunk_split<kSelN0, kEnc>(mk, a_base, b01, b2, pr, pc, lane, acc);
     else
-      chunk_hybrid<kSelN1, 3, kEnc>(a_base, b01, b2, pr, pc, lane, acc);
+      chunk_split<kSelN1, kEnc>(mk, a_base, b01, b2, pr, pc, lane, acc);
   } else if (sel == kSelAll) {
     chunk_mma<kSelAll, kEnc>(a_base, b01, b2, pr, pc, lane, ksteps, acc);
   } else if (sel == kSelN0) {
@@ -453,14 +567,17 @@ __device__ __forceinline__ void product_chunk(CorrSmem& sm, int buf, int warp, i
 }
 
 // kMode: kSingle = one frame (args), kBatch = per-frame descriptors, kGated =
-// descriptors plus hold bits (a gated (tile, gate) group's segments).
-enum : int { kSingle = 0, kBatch = 1, kGated = 2 };
+// descriptors plus hold bits (a gated (tile, gate) group's segments),
+// kGateArith = one descriptor per gate, each item a (band, tile, gate) whose
+// chunks and rows follow from the gate arithmetic above.
+enum : int { kSingle = 0, kBatch = 1, kGated = 2, kGateArith = 3 };
 
-template <int kMode, bool kEnc>
+template <int kMode, bool kEnc, int kSplitT = -1>
 __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                 CorrArgs args) {
   constexpr bool kFrames = kMode != kSingle;
   constexpr bool kHold = kMode == kGated;
+  constexpr bool kArith = kMode == kGateArith;
   extern __shared__ uint8_t smem_raw[];
   CorrSmem& sm = *reinterpret_cast<CorrSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                               ~static_cast<uintptr_t>(127));
@@ -484,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
     const int uw = warp - kMmaWarps;  // 0..3
     const bool producer = uw == 0 && lane == 0;
     const int eg = lane & 15, p = lane >> 4, tg = 2 * uw + p;  // samples 16tg..16tg+15 of each chunk
-    Walk<kFrames, kHold> ld;  // the TMA issuer walks the same units, kStages ahead
+    Walk<kFrames, kHold, kArith> ld;  // the TMA issuer walks the same units, kStages ahead
     ld.start(args);
     uint32_t issued = 0;
     const CUtensorMap* fenced = nullptr;
@@ -500,9 +617,14 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
         ChunkMeta& m = sm.meta[s];
         m.f = ld.f;
         m.bij = ld.bi | (ld.bj << 16);
-        m.lo = ld.T0 - ld.c * kTC;
-        m.hi = ld.T - ld.c * kTC;
-        m.flags = kMetaValid | ((ld.c + 1 == ld.c1 && !ld.hold) ? kMetaEnd : 0) | (ld.mode << 4);
+        if (kArith) {
+          gate_windows(ld.c, ld.T, ld.gP, ld.gphase, ld.ga, ld.gb, m);
+        } else {
+          m.lo = ld.T0 - ld.c * kTC;
+          m.hi = ld.T - ld.c * kTC;
+          m.lo2 = m.hi2 = 0;
+        }
+        m.flags = kMetaValid | ((ld.last() && !ld.hold) ? kMetaEnd : 0) | (ld.mode << 4);
         m.N = ld.fN;
         m.B = ld.fB;
         m.vis = ld.fvis;
@@ -547,7 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
           break;
         }
         const ChunkMeta& m = sm.meta[s];
-        const int flags = m.flags, bij = m.bij, lo = m.lo, hi = m.hi;
+        const int flags = m.flags, bij = m.bij, lo = m.lo, hi = m.hi, lo2 = m.lo2, hi2 = m.hi2;
         if (threadIdx.x == kMmaWarps * 32) sm.pmeta[buf] = m;  // passed on with the planes
         if (!(flags & kMetaValid)) {
           mbar_arrive(&sm.pfull[buf]);
@@ -564,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
           if (lo <= 0 && hi >= kTC)
             unpack_unit<false, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, 0, kTC);
           else
-            unpack_unit<true, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi);
+            unpack_unit<true, kEnc>(box, pl0, pl1, pl2, j == 1, eg, tg, p, lo, hi, lo2, hi2);
         }
         mbar_arrive(&sm.pfull[buf]);
         mbar_arrive(&sm.bempty[s]);
@@ -642,8 +764,10 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       const int flags = m.flags;
       if (!(flags & kMetaValid)) return;  // end of this CTA's chunks
       const int bi = m.bij & 0xFFFF, bj = m.bij >> 16;
+      // rows past the last valid one are masked to zero: their k-steps can be skipped
+      const int nvalid = m.hi2 > m.lo2 ? max(m.hi, m.hi2) : m.hi;
       int pr, pc, sel;
-      product_chunk<kEnc>(sm, buf, warp, lane, bi == bj, m.hi, args.hybrid, pr, pc, sel, acc);
+      product_chunk<kEnc, kSplitT>(sm, buf, warp, lane, bi == bj, nvalid, args.hybrid, it, pr, pc, sel, acc);
       // the writer's fields, read before the buffer (and its metadata) is released
       const int f = m.f, N = m.N;
       const int64_t B = m.B;
@@ -665,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       return;
     }
     int pr, pc, sel;
-    product_chunk<kEnc>(sm, buf, warp, lane, diag, x.T - x.c * kTC, args.hybrid, pr, pc, sel, acc);
+    product_chunk<kEnc, kSplitT>(sm, buf, warp, lane, diag, x.T - x.c * kTC, args.hybrid, it, pr, pc, sel, acc);
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.pempty[buf]);
     if (x.c + 1 == x.c1) {  // end of the item: write it
@@ -681,16 +805,18 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
   }
 }
 
-// Copy frames whose rows are not 16-byte aligned into an aligned staging
-// buffer [T][F][Np] (Np = N rounded up to 16); padding bytes are 0x88.
+// Copy the bands [f0, f0 + F) of a frame [T][F_in][N] whose rows are not
+// 16-byte aligned into an aligned staging buffer [T][F][Np] (Np = N rounded
+// up to 16); padding bytes are 0x88. rows = T * F.
 __global__ void repack_rows_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst, int64_t rows,
-                                   int32_t N, int32_t Np) {
+                                   int32_t N, int32_t Np, int32_t F, int32_t F_in, int32_t f0) {
   const int64_t total = rows * Np;
   for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < total;
        k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t r = k / Np;
     const int32_t e = static_cast<int32_t>(k - r * Np);
-    dst[k] = e < N ? src[r * N + e] : static_cast<uint8_t>(0x88);
+    const int64_t t = r / F, f = r - t * F;
+    dst[k] = e < N ? src[(t * F_in + f0 + f) * N + e] : static_cast<uint8_t>(0x88);
   }
 }
 

@@ -24,15 +24,17 @@ constexpr int kSumRows = 2048;    // time rows per block of the running-sum kern
 constexpr int kSumThreads = 256;
 
 // sums[f][i] = {sum_t Xr[t][f][i], sum_t Xi[t][f][i]} over rows [0, T), added
-// atomically (the caller zeroes sums). Frame rows hold F bands of Np bytes
-// (Np % 4 == 0, 4-byte aligned); elements i >= N are skipped. Thread x reads
-// word x of every row of its block's time range.
+// atomically (the caller zeroes sums). Time row t starts row_bytes * t bytes
+// after `frame` and holds F bands of Np bytes (Np % 4 == 0, row_bytes % 4 ==
+// 0, 4-byte aligned); elements i >= N are skipped. Thread x reads word x of
+// every row of its block's time range.
 __global__ void __launch_bounds__(kSumThreads) nibble_sums_kernel(const uint8_t* __restrict__ frame, int32_t N,
                                                                   int32_t Np, int32_t F, int32_t T,
-                                                                  int32_t* __restrict__ sums) {
-  const int64_t W = static_cast<int64_t>(F) * (Np / 4);  // words per row
+                                                                  int64_t row_bytes, int32_t* __restrict__ sums) {
+  const int64_t Wr = static_cast<int64_t>(F) * (Np / 4);  // words per row read
+  const int64_t W = row_bytes / 4;                        // words between time rows
   const int64_t x = static_cast<int64_t>(blockIdx.x) * kSumThreads + threadIdx.x;
-  if (x >= W) return;
+  if (x >= Wr) return;
   const int32_t t0 = static_cast<int32_t>(blockIdx.y) * kSumRows;
   const int32_t t1 = min(T, t0 + kSumRows);
   const uint32_t* col = reinterpret_cast<const uint32_t*>(frame) + x;

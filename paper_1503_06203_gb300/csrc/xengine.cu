@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <vector>
 
 #include "xengine.h"
+#include "xe_batch.cuh"
 #include "xe_corr.cuh"
 #include "xe_lags.cuh"
 #include "xe_offsets.cuh"
@@ -62,8 +64,12 @@ int device_setup(int dev) {
   if (g_dev_ready[dev]) return CORR_OK;
   cudaError_t e = cudaSuccess;
   for (const void* k : {reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit7>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit5>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit4>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGated, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGateArith, false>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, true>)})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
@@ -101,8 +107,19 @@ int product_hybrid() {
 const int g_hybrid = product_hybrid();
 
 int effective_product(int product) { return product < 0 ? g_hybrid : product; }
-// The kernel's chunk path: 1 = tensor cores + dp4a, 0 = tensor cores only.
-int chunk_hybrid_flag(int product) { return effective_product(product) == 0 ? 0 : 1; }
+// The kernel's split of each chunk (xe::kSplit*): tensor cores only for
+// product 0, else `mma_steps` of every 8 k-steps of 32 samples on the tensor
+// cores (CORR_OPT_MMA_STEPS) and the rest on dp4a.
+int chunk_hybrid_flag(int product, int mma_steps) {
+  if (effective_product(product) == 0) return xe::kSplitMma;
+  switch (mma_steps) {
+    case 8: return xe::kSplitMma;
+    case 7: return xe::kSplit7;
+    case 5: return xe::kSplit5;
+    case 4: return xe::kSplit4;
+    default: return xe::kSplit6;
+  }
+}
 
 // Upper-triangle tile order: block rows bi <= block columns bj, row-major (Fig. 1).
 void triangle_tiles(int32_t N, int32_t tile, std::vector<int32_t>& bi, std::vector<int32_t>& bj) {
@@ -128,6 +145,8 @@ struct Plan {
 // ---- the handle ----------------------------------------------------------------
 struct corr_handle {
   int32_t N = 0, F = 0, T = 0;
+  // input frames hold F_in bands; the handle correlates bands [f0, f0 + F) of them
+  int32_t F_in = 0, f0 = 0;
   int64_t B = 0;
   int device = 0;
   int32_t* acc = nullptr;  // [F][B][2]
@@ -137,6 +156,7 @@ struct corr_handle {
   int64_t launches = 0;    // kernels launched by this handle
   int product = -1;        // CORR_OPT_PRODUCT (-1: library default)
   int split_opt = 0;       // CORR_OPT_SPLIT (0: automatic)
+  int mma_steps = 6;       // CORR_OPT_MMA_STEPS: tensor-core k-steps per 8 (the rest on dp4a)
   int sticky = CORR_OK;
   int32_t* d_err = nullptr;
   cudaEvent_t last = nullptr;
@@ -154,6 +174,10 @@ struct corr_handle {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
   // offset-encoded route: per-element nibble sums [F][N][2] of the current launch
   int32_t* d_sums = nullptr;
+  // corr_status: a private stream and a pinned word to read the fault word
+  // after the handle's last call only (not after unrelated work)
+  cudaStream_t s_status = nullptr;
+  int32_t* h_status = nullptr;
 };
 
 namespace {
@@ -273,12 +297,16 @@ void free_plan(Plan* pl) {
   *pl = Plan();
 }
 
+// 3-D map (elements, bands, time) of F bands of Np bytes starting at `base`;
+// consecutive time samples are row_bytes apart (0: F * Np, a frame of exactly
+// these bands). Elements past Np and samples past T read as zero bytes.
 int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_t T, uint32_t box_n = xe::kTile,
-              uint32_t box_t = xe::kTC) {
+              uint32_t box_t = xe::kTC, int64_t row_bytes = 0) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return fail(CORR_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  if (row_bytes == 0) row_bytes = static_cast<int64_t>(Np) * F;
   cuuint64_t dims[3] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(F), static_cast<cuuint64_t>(T)};
-  cuuint64_t strides[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(Np) * static_cast<cuuint64_t>(F)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(Np), static_cast<cuuint64_t>(row_bytes)};
   cuuint32_t box[3] = {static_cast<cuuint32_t>(box_n), 1u, static_cast<cuuint32_t>(box_t)};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(base), dims, strides, box, estr,
@@ -307,10 +335,12 @@ int check_handle(corr_handle* h) {
   return CORR_OK;
 }
 
-// Launch the correlator over a [T][F][Np] device frame (16-byte aligned rows).
-int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& pl, cudaStream_t st) {
+// Launch the correlator over the handle's F bands of Np bytes (16-byte
+// aligned rows) at `frame`, time samples row_bytes apart.
+int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, int64_t row_bytes, const Plan& pl,
+                 cudaStream_t st) {
   CUtensorMap tm;
-  int rc = make_tmap(&tm, frame, Np, h->F, pl.T);
+  int rc = make_tmap(&tm, frame, Np, h->F, pl.T, xe::kTile, xe::kTC, row_bytes);
   if (rc) return rc;
   const bool enc = effective_product(h->product) == 2;
   if (enc) {
@@ -328,7 +358,7 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
     XE_CHECK(h, cudaMemsetAsync(h->d_sums, 0, sbytes, st));
     const int64_t words = static_cast<int64_t>(h->F) * (Np / 4);
     const dim3 sg(static_cast<unsigned>(ceil_div(words, xe::kSumThreads)), static_cast<unsigned>(ceil_div(pl.T, xe::kSumRows)));
-    xe::nibble_sums_kernel<<<sg, xe::kSumThreads, 0, st>>>(frame, h->N, Np, h->F, pl.T, h->d_sums);
+    xe::nibble_sums_kernel<<<sg, xe::kSumThreads, 0, st>>>(frame, h->N, Np, h->F, pl.T, row_bytes, h->d_sums);
     XE_CHECK(h, cudaGetLastError());
     xe::offset_seed_kernel<<<static_cast<unsigned>(static_cast<int64_t>(h->F) * h->N), 256, 0, st>>>(
         h->d_sums, h->N, h->B, pl.T, h->fresh ? 0 : 1, h->acc);
@@ -347,10 +377,16 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   a.B = h->B;
   a.vis = h->acc;
   a.fresh = h->fresh ? 1 : 0;
-  a.hybrid = chunk_hybrid_flag(h->product);
+  a.hybrid = chunk_hybrid_flag(h->product, h->mma_steps);
   a.err = h->d_err;
-  if (enc)
+  if (enc)  // (the offset-encoded route splits 96 / 32 or runs tensor cores only)
     xe::corr_tile_kernel<xe::kSingle, true><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  else if (a.hybrid == xe::kSplit7)
+    xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit7><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  else if (a.hybrid == xe::kSplit5)
+    xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit5><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
+  else if (a.hybrid == xe::kSplit4)
+    xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit4><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   else
     xe::corr_tile_kernel<xe::kSingle, false><<<pl.grid, xe::kThreads, kSmemBytes, st>>>(tm, a);
   XE_CHECK(h, cudaGetLastError());
@@ -359,9 +395,13 @@ int launch_frame(corr_handle* h, const uint8_t* frame, int32_t Np, const Plan& p
   return CORR_OK;
 }
 
-corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
+// A handle for bands [f0, f0 + F) of frames with F_in bands.
+corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev, int32_t F_in, int32_t f0) {
   if (N < 1 || N > CORR_MAX_N) return fail(CORR_EINVAL, "N=%d outside [1, %d]", N, CORR_MAX_N), nullptr;
   if (F < 1) return fail(CORR_EINVAL, "F=%d must be >= 1", F), nullptr;
+  if (f0 < 0 || F_in < 1 || static_cast<int64_t>(f0) + F > F_in)
+    return fail(CORR_EINVAL, "bands [%d, %lld) do not lie within a frame of %d bands", f0,
+                static_cast<long long>(f0) + F, F_in), nullptr;
   if (T < 1 || T > CORR_MAX_SAMPLES) return fail(CORR_EINVAL, "T=%d outside [1, %d]", T, CORR_MAX_SAMPLES), nullptr;
   const int64_t B = static_cast<int64_t>(N) * (N + 1) / 2;
   const int64_t nb = static_cast<int64_t>(ceil_div(N, xe::kTile));
@@ -379,6 +419,8 @@ corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
   h->N = N;
   h->F = F;
   h->T = T;
+  h->F_in = F_in;
+  h->f0 = f0;
   h->B = B;
   h->device = dev;
   const size_t acc_bytes = static_cast<size_t>(F) * B * 2 * sizeof(int32_t);
@@ -411,13 +453,16 @@ corr_handle_t* create_impl(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
   return h;
 }
 
-// Frames whose rows are not 16-byte aligned go through the staging buffer.
+// The handle's bands of an input frame [T][F_in][N]: in place when its rows
+// are 16-byte aligned (*frame = the first of the handle's bands, time samples
+// *row_bytes apart), else copied into the staging buffer [T][F][Np].
 int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t st, const uint8_t** frame,
-                    int32_t* Np) {
+                    int32_t* Np, int64_t* row_bytes) {
   const bool aligned = (h->N % 16 == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
   if (aligned) {
-    *frame = in;
+    *frame = in + static_cast<size_t>(h->f0) * h->N;
     *Np = h->N;
+    *row_bytes = static_cast<int64_t>(h->F_in) * h->N;
     return CORR_OK;
   }
   const int32_t np = static_cast<int32_t>(ceil_div(h->N, 16) * 16);
@@ -440,12 +485,13 @@ int stage_if_needed(corr_handle* h, const uint8_t* in, int32_t T, cudaStream_t s
   const int64_t total = rows * np;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>(ceil_div(total, threads), int64_t(g_sms[h->device]) * 8);
-  xe::repack_rows_kernel<<<static_cast<int>(std::max<int64_t>(blocks, 1)), threads, 0, st>>>(in, h->stage, rows,
-                                                                                          h->N, np);
+  xe::repack_rows_kernel<<<static_cast<int>(std::max<int64_t>(blocks, 1)), threads, 0, st>>>(
+      in, h->stage, rows, h->N, np, h->F, h->F_in, h->f0);
   XE_CHECK(h, cudaGetLastError());
   ++h->launches;
   *frame = h->stage;
   *Np = np;
+  *row_bytes = static_cast<int64_t>(np) * h->F;
   return CORR_OK;
 }
 
@@ -522,7 +568,8 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
   return CORR_OK;
 }
 
-int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid, bool gated) {
+// kind: 1 = gate segments (corr_tile_kernel<kGated>), 2 = gate arithmetic (<kGateArith>).
+int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid, int kind) {
   if (b.exec) {
     cudaGraphExecDestroy(b.exec);
     b.exec = nullptr;
@@ -553,8 +600,8 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = gated ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>)
-                  : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false>);
+  kp.func = kind == 2 ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false>)
+                      : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -570,8 +617,145 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   b.key_items = nitems;
   b.key_grid = grid;
   b.key_hybrid = hybrid;
-  b.key_gated = gated ? 1 : 0;
+  b.key_gated = kind;
   b.key_err = err;
+  return CORR_OK;
+}
+
+// ---- batched launches: a ring of launch sets, each a graph instantiated once ----
+// A set holds one launch's frame descriptors and frame order (pinned host
+// block, copied by the graph's first node), its work list (device, written
+// by the plan kernel, the second node) and the correlator (third node).
+// Launches update the nodes' parameters; the graph is never rebuilt. The
+// host writes a set only after the launch that last read it has finished,
+// and waits for that only when every set of the ring is in flight.
+constexpr int kBatchSets = 4;
+constexpr size_t kDescBytes = sizeof(xe::FrameDesc) * kMaxBatchFrames;
+constexpr size_t kFirstOff = (kDescBytes + 255) / 256 * 256;                   // int64 first[n + 1]
+constexpr size_t kOrderOff = kFirstOff + sizeof(int64_t) * (kMaxBatchFrames + 1);  // int32 order[n]
+constexpr size_t kBlockBytes = (kOrderOff + sizeof(int32_t) * kMaxBatchFrames + 255) / 256 * 256;
+
+struct RingSet {
+  uint8_t* h_blk = nullptr;  // pinned
+  uint8_t* d_blk = nullptr;
+  int4* d_items = nullptr;   // stream-ordered allocation
+  size_t cap_items = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  cudaGraph_t graph = nullptr;  // kept: its node handles address the nodes of `exec` in updates
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t n_copy = nullptr, n_plan = nullptr, n_corr = nullptr;
+  int key_hybrid = -1;
+  // kernel arguments (the graph's kernel nodes read them when their parameters are set)
+  const xe::FrameDesc* p_frames = nullptr;
+  const int64_t* p_first = nullptr;
+  const int32_t* p_order = nullptr;
+  int32_t p_nframes = 0;
+  int4* p_items = nullptr;
+  int64_t p_nitems = 0, p_grid = 0;
+  CUtensorMap p_unused;
+  xe::CorrArgs p_args;
+};
+
+struct BatchRing {
+  RingSet set[kBatchSets];
+  int next = 0;
+};
+
+BatchRing* g_ring[64];  // per device, kept for the life of the process (guarded by g_batch_mu)
+
+int ring_set_init(RingSet& r) {
+  if (r.h_blk) return CORR_OK;
+  cudaError_t e = cudaMallocHost(&r.h_blk, kBlockBytes);
+  if (e != cudaSuccess) {
+    r.h_blk = nullptr;
+    return alloc_failed("batch descriptor block (pinned)", kBlockBytes, e);
+  }
+  e = cudaMalloc(&r.d_blk, kBlockBytes);
+  if (e != cudaSuccess) {
+    r.d_blk = nullptr;
+    return alloc_failed("batch descriptor block", kBlockBytes, e);
+  }
+  if (cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming) != cudaSuccess) return fail(CORR_ECUDA, "batch event");
+  memset(&r.p_unused, 0, sizeof r.p_unused);
+  return CORR_OK;
+}
+
+// Work-list capacity, grown by doubling with stream-ordered allocation (no
+// device-wide synchronisation). The old list is freed after the set's last launch.
+int ring_set_items(RingSet& r, int64_t nitems, cudaStream_t st) {
+  if (static_cast<size_t>(nitems) <= r.cap_items) return CORR_OK;
+  size_t cap = std::max<size_t>(r.cap_items * 2, 1 << 16);
+  while (cap < static_cast<size_t>(nitems)) cap *= 2;
+  cudaError_t e;
+  if (r.d_items) {
+    if ((e = cudaStreamWaitEvent(st, r.done, 0)) != cudaSuccess) return fail(CORR_ECUDA, "batch: %s", cudaGetErrorString(e));
+    if ((e = cudaFreeAsync(r.d_items, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch: %s", cudaGetErrorString(e));
+    r.d_items = nullptr;
+    r.cap_items = 0;
+  }
+  e = cudaMallocAsync(reinterpret_cast<void**>(&r.d_items), cap * sizeof(int4), st);
+  if (e != cudaSuccess) {
+    r.d_items = nullptr;
+    return alloc_failed("batch work list", cap * sizeof(int4), e);
+  }
+  r.cap_items = cap;
+  return CORR_OK;
+}
+
+void* corr_kernel_fn(int hybrid) {
+  (void)hybrid;  // batched launches run kSplitMma or kSplit6, chosen at run time
+  return reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false>);
+}
+
+// Set the three nodes' parameters from r.p_* (and build the graph the first time).
+int ring_set_launch(RingSet& r, int hybrid, cudaStream_t st) {
+  const unsigned plan_blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(r.p_nitems, 256), 4096));
+  void* plan_params[7] = {&r.p_frames, &r.p_first, &r.p_order, &r.p_nframes, &r.p_items, &r.p_nitems, &r.p_grid};
+  void* corr_params[2] = {&r.p_unused, &r.p_args};
+  cudaKernelNodeParams kp_plan, kp_corr;
+  memset(&kp_plan, 0, sizeof kp_plan);
+  kp_plan.func = reinterpret_cast<void*>(xe::batch_plan_kernel);
+  kp_plan.gridDim = dim3(plan_blocks);
+  kp_plan.blockDim = dim3(256);
+  kp_plan.kernelParams = plan_params;
+  memset(&kp_corr, 0, sizeof kp_corr);
+  kp_corr.func = corr_kernel_fn(hybrid);
+  kp_corr.gridDim = dim3(static_cast<unsigned>(r.p_grid));
+  kp_corr.blockDim = dim3(xe::kThreads);
+  kp_corr.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
+  kp_corr.kernelParams = corr_params;
+  cudaError_t e = cudaSuccess;
+  if (r.exec) {  // update the instantiated graph in place; rebuild it if the update is refused
+    e = cudaGraphExecKernelNodeSetParams(r.exec, r.n_plan, &kp_plan);
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(r.exec, r.n_corr, &kp_corr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(r.exec);
+      cudaGraphDestroy(r.graph);
+      r.exec = nullptr;
+      r.graph = nullptr;
+    }
+  }
+  if (!r.exec) {
+    cudaGraph_t g = nullptr;
+    e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess)
+      e = cudaGraphAddMemcpyNode1D(&r.n_copy, g, nullptr, 0, r.d_blk, r.h_blk, kBlockBytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&r.n_plan, g, &r.n_copy, 1, &kp_plan);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&r.n_corr, g, &r.n_plan, 1, &kp_corr);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&r.exec, g, 0);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      r.exec = nullptr;
+      return fail(CORR_ECUDA, "building the batch graph: %s", cudaGetErrorString(e));
+    }
+    r.graph = g;
+  }
+  r.key_hybrid = hybrid;
+  if ((e = cudaGraphLaunch(r.exec, st)) != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+  if ((e = cudaEventRecord(r.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
+  r.pending = true;
   return CORR_OK;
 }
 
@@ -595,83 +779,189 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
       if (hs[j] == hs[k]) return fail(CORR_EINVAL, "batch handles must be distinct (frames %d and %d)", j, k);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // work list: whole tiles of every frame, costed by their integration length
-  struct It {
-    int4 w;
-    double cost;
-  };
-  std::vector<It> work;
-  for (int k = 0; k < n; ++k) {
-    std::vector<int32_t> bi, bj;
-    triangle_tiles(hs[k]->N, xe::kTile, bi, bj);
-    const int32_t nch = static_cast<int32_t>(ceil_div(Ts ? Ts[k] : hs[k]->T, xe::kTC));
-    for (int32_t f = 0; f < hs[k]->F; ++f)
-      for (size_t u = 0; u < bi.size(); ++u)
-        work.push_back({make_int4(f | (k << 20), bi[u] | (bj[u] << 16), 0, nch),
-                        (bi[u] == bj[u] ? kDiagCost : 1.0) * nch});
-  }
-  std::stable_sort(work.begin(), work.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
   const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
-  const int64_t nitems = static_cast<int64_t>(work.size());
-  const int64_t grid = std::min<int64_t>(slots, nitems);
+  // Per frame: tiles, chunks, and a time split that keeps its items short
+  // against a CTA's share of the whole batch (a frame with few tiles and a
+  // long time axis is cut into ranges, written with atomic adds), so the
+  // launch's tail is not set by one long tile.
+  std::vector<int64_t> tiles(n), nch(n), per(n), ranges(n);
+  double work = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const int64_t nb = ceil_div(hs[k]->N, xe::kTile);
+    tiles[k] = nb * (nb + 1) / 2 * hs[k]->F;
+    nch[k] = ceil_div(Ts ? Ts[k] : hs[k]->T, xe::kTC);
+    work += static_cast<double>(hs[k]->F) * (nb * (nb - 1) / 2 + kDiagCost * nb) * nch[k];
+  }
+  const double share = work / static_cast<double>(slots);  // chunks per CTA, evenly spread
+  int64_t nitems = 0;
+  for (int k = 0; k < n; ++k) {
+    int64_t s = static_cast<int64_t>(std::ceil(static_cast<double>(nch[k]) / std::max(1.0, share / 4.0)));
+    s = std::max<int64_t>(1, std::min<int64_t>({s, nch[k], 64}));
+    per[k] = ceil_div(nch[k], s);
+    ranges[k] = ceil_div(nch[k], per[k]);
+    nitems += tiles[k] * ranges[k];
+  }
   if (nitems > INT32_MAX) return fail(CORR_EINVAL, "batch work list too long");
+  const int64_t grid = std::min<int64_t>(slots, nitems);
+  // frames by the chunks of their items, longest first (stable: frame order breaks ties)
+  std::vector<int32_t> order(n);
+  for (int k = 0; k < n; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return per[a] > per[b]; });
 
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  if (!g_batch[dev]) g_batch[dev] = new (std::nothrow) BatchCtx;
-  if (!g_batch[dev]) return fail(CORR_ENOMEM, "batch context");
-  BatchCtx& ctx = *g_batch[dev];
-  BatchSet& b = ctx.set[ctx.next];
-  if (b.pending) {  // the graph launch that last read these pinned buffers must be done
-    cudaError_t e = cudaEventSynchronize(b.done);
-    if (e != cudaSuccess) return fail(CORR_ECUDA, "waiting for a previous batch: %s", cudaGetErrorString(e));
-    b.pending = false;
-  }
-  int rc = grow_set(b, static_cast<size_t>(n), static_cast<size_t>(nitems));
+  if (!g_ring[dev]) g_ring[dev] = new (std::nothrow) BatchRing;
+  if (!g_ring[dev]) return fail(CORR_ENOMEM, "batch ring");
+  BatchRing& ring = *g_ring[dev];
+  RingSet& r = ring.set[ring.next];
+  int rc = ring_set_init(r);
   if (rc) return rc;
-  // snake layout: position r*grid + c is CTA c's r-th item; row r runs forward or backward
-  for (int64_t i = 0; i < nitems; ++i) {
-    const int64_t r = i / grid, c = i % grid;
-    const int64_t col = (r & 1) ? grid - 1 - c : c;
-    const int64_t pos = r * grid + col;
-    b.h_items[pos < nitems ? pos : i] = work[i].w;
+  if (r.pending) {  // the launch that last read this set's pinned block must be done
+    cudaError_t e = cudaEventSynchronize(r.done);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "waiting for a previous batch: %s", cudaGetErrorString(e));
+    r.pending = false;
   }
-  // with a ragged last row the snake's backward row may point past the end: redo it in order
-  if (nitems % grid != 0 && ((nitems / grid) & 1)) {
-    const int64_t r = nitems / grid;
-    for (int64_t i = r * grid; i < nitems; ++i) b.h_items[i] = work[i].w;
+  if ((rc = ring_set_items(r, nitems, st))) return rc;
+  xe::FrameDesc* desc = reinterpret_cast<xe::FrameDesc*>(r.h_blk);
+  int64_t* first = reinterpret_cast<int64_t*>(r.h_blk + kFirstOff);
+  int32_t* ord = reinterpret_cast<int32_t*>(r.h_blk + kOrderOff);
+  int64_t acc_items = 0;
+  for (int s = 0; s < n; ++s) {
+    first[s] = acc_items;
+    ord[s] = order[s];
+    acc_items += tiles[order[s]] * ranges[order[s]];
   }
+  first[n] = acc_items;
   for (int k = 0; k < n; ++k) {
     corr_handle* h = hs[k];
     const int32_t Tk = Ts ? Ts[k] : h->T;
     if ((rc = order_after_last(h, st))) return rc;
     const uint8_t* frame;
     int32_t np;
-    if ((rc = stage_if_needed(h, inputs[k], Tk, st, &frame, &np))) return rc;
-    xe::FrameDesc& d = b.h_desc[k];
-    if ((rc = make_tmap(&d.map, frame, np, h->F, Tk))) return rc;
+    int64_t row_bytes;
+    if ((rc = stage_if_needed(h, inputs[k], Tk, st, &frame, &np, &row_bytes))) return rc;
+    xe::FrameDesc& d = desc[k];
+    if ((rc = make_tmap(&d.map, frame, np, h->F, Tk, xe::kTile, xe::kTC, row_bytes))) return rc;
+    if (ranges[k] > 1 && h->fresh) {  // time-split items add atomically onto zeros
+      XE_CHECK(h, cudaMemsetAsync(h->acc, 0, static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t), st));
+      h->fresh = false;
+    }
     d.N = h->N;
     d.T = Tk;
-    d.nch = static_cast<int32_t>(ceil_div(Tk, xe::kTC));
+    d.nch = static_cast<int32_t>(nch[k]);
     d.fresh = h->fresh ? 1 : 0;
     d.B = h->B;
     d.vis = h->acc;
     d.t0 = 0;
     d.atomic = 0;
+    d.F = h->F;
+    d.nb = static_cast<int32_t>(ceil_div(h->N, xe::kTile));
+    d.per = static_cast<int32_t>(per[k]);
   }
-  const int hybrid = chunk_hybrid_flag(hs[0]->product);
-  if (!b.exec || b.key_frames != n || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
-      b.key_gated != 0 || b.key_err != hs[0]->d_err)
-    if ((rc = build_graph(b, n, nitems, grid, hs[0]->d_err, hybrid, false))) return rc;
+  const int hybrid = chunk_hybrid_flag(hs[0]->product, hs[0]->mma_steps);
+  r.p_frames = reinterpret_cast<const xe::FrameDesc*>(r.d_blk);
+  r.p_first = reinterpret_cast<const int64_t*>(r.d_blk + kFirstOff);
+  r.p_order = reinterpret_cast<const int32_t*>(r.d_blk + kOrderOff);
+  r.p_nframes = n;
+  r.p_items = r.d_items;
+  r.p_nitems = nitems;
+  r.p_grid = grid;
+  xe::CorrArgs& a = r.p_args;
+  a.items = r.d_items;
+  a.frames = r.p_frames;
+  a.nitems = static_cast<int32_t>(nitems);
+  a.nch = 0;
+  a.T = 0;
+  a.N = 0;
+  a.B = 0;
+  a.vis = nullptr;
+  a.fresh = 0;
+  a.hybrid = hybrid == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
+  a.err = hs[0]->d_err;
+  if ((rc = ring_set_launch(r, hybrid, st))) return rc;
+  ring.next = (ring.next + 1) % kBatchSets;
+  for (int k = 0; k < n; ++k) {
+    hs[k]->fresh = false;
+    hs[k]->samples += Ts ? Ts[k] : hs[k]->T;
+    hs[k]->launches += 2;  // the handle's frame ran in one (shared) plan and correlator launch
+    if ((rc = record_last(hs[k], st))) return rc;
+  }
+  return CORR_OK;
+}
+
+// ---- gated correlation, gate windows by arithmetic ---------------------------------
+// One descriptor per gate (the same frame map, the gate's accumulators and
+// fresh flag, the gate arithmetic), one item per (band, tile, gate) over the
+// whole frame; the kernel visits only the chunks that hold samples of the
+// item's gate and masks the other rows. Items are dealt round-robin in
+// (band, gate, tile) order, so CTAs running together share a band's input.
+int gated_arith_launch(corr_handle_t* const* gates, int G, const CUtensorMap& map, int32_t T, int32_t period,
+                       int32_t phase, const std::vector<int64_t>& per_gate, const std::vector<int32_t>& gate_fresh,
+                       cudaStream_t st) {
+  corr_handle* h0 = gates[0];
+  if (G >= kMaxBatchFrames) return fail(CORR_EINVAL, "gated: at most %d gates", kMaxBatchFrames - 1);
+  std::vector<int32_t> bi, bj;
+  triangle_tiles(h0->N, xe::kTile, bi, bj);
+  const int32_t nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
+  int live = 0;
+  for (int g = 0; g < G; ++g) live += per_gate[g] > 0;
+  const int64_t nitems = static_cast<int64_t>(h0->F) * live * static_cast<int64_t>(bi.size());
+  if (nitems == 0) return CORR_OK;
+  if (nitems > INT32_MAX || h0->F >= (1 << 20)) return fail(CORR_EINVAL, "gated: work list too large");
+  const int dev = h0->device;
+  const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
+  const int64_t grid = std::min<int64_t>(slots, nitems);
+
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (!g_batch[dev]) g_batch[dev] = new (std::nothrow) BatchCtx;
+  if (!g_batch[dev]) return fail(CORR_ENOMEM, "batch context");
+  BatchCtx& ctx = *g_batch[dev];
+  BatchSet& b = ctx.set[ctx.next];
+  if (b.pending) {
+    cudaError_t e = cudaEventSynchronize(b.done);
+    if (e != cudaSuccess) return fail(CORR_ECUDA, "waiting for a previous batch: %s", cudaGetErrorString(e));
+    b.pending = false;
+  }
+  int rc = grow_set(b, static_cast<size_t>(G), static_cast<size_t>(nitems));
+  if (rc) return rc;
+  int64_t k = 0;
+  for (int32_t f = 0; f < h0->F; ++f)
+    for (int g = 0; g < G; ++g) {
+      if (per_gate[g] == 0) continue;
+      for (size_t u = 0; u < bi.size(); ++u)
+        b.h_items[k++] = make_int4(f | (g << 20), bi[u] | (bj[u] << 16), 0, nch);
+    }
+  for (int g = 0; g < G; ++g) {
+    xe::FrameDesc& d = b.h_desc[g];
+    d.map = map;
+    d.N = h0->N;
+    d.T = T;
+    d.nch = nch;
+    d.fresh = gate_fresh[g];
+    d.B = h0->B;
+    d.vis = gates[g]->acc;
+    d.t0 = 0;
+    d.atomic = 0;
+    d.F = h0->F;
+    d.nb = static_cast<int32_t>(ceil_div(h0->N, xe::kTile));
+    d.per = nch;
+    d.period = period;
+    d.phase = phase;
+    d.G = G;
+    d.gate = g;
+  }
+  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps) == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
+  if (!b.exec || b.key_frames != G || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
+      b.key_gated != 2 || b.key_err != h0->d_err)
+    if ((rc = build_graph(b, G, nitems, grid, h0->d_err, hybrid, 2))) return rc;
   cudaError_t e = cudaGraphLaunch(b.exec, st);
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
   if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
   b.pending = true;
   ctx.next ^= 1;
-  for (int k = 0; k < n; ++k) {
-    hs[k]->fresh = false;
-    hs[k]->samples += Ts ? Ts[k] : hs[k]->T;
-    ++hs[k]->launches;  // the handle's frame ran in one (shared) launch
-    if ((rc = record_last(hs[k], st))) return rc;
+  for (int g = 0; g < G; ++g) {
+    gates[g]->samples += per_gate[g];
+    ++gates[g]->launches;
+    if ((rc = record_last(gates[g], st))) return rc;
   }
   return CORR_OK;
 }
@@ -690,12 +980,16 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
   for (int g = 0; g < G; ++g) {
     int rc = check_handle(gates[g]);
     if (rc) return rc;
-    if (gates[g]->N != gates[0]->N || gates[g]->F != gates[0]->F || gates[g]->device != gates[0]->device)
-      return fail(CORR_EINVAL, "gated: gate handles must share N, F and the device");
+    if (gates[g]->N != gates[0]->N || gates[g]->F != gates[0]->F || gates[g]->F_in != gates[0]->F_in ||
+        gates[g]->f0 != gates[0]->f0 || gates[g]->device != gates[0]->device)
+      return fail(CORR_EINVAL, "gated: gate handles must share N, the bands and the device");
     for (int j = 0; j < g; ++j)
       if (gates[j] == gates[g]) return fail(CORR_EINVAL, "gated: gate handles must be distinct");
   }
   corr_handle* h0 = gates[0];
+  // periods of at least one chunk (and small enough for 32-bit gate positions)
+  // take the gate-arithmetic kernel: one item per (band, tile, gate)
+  const bool arith = period >= xe::kTC && period <= (1 << 29);
   // segments, found from the gate boundaries within a period
   struct Seg {
     int32_t t0, t1, g;
@@ -707,7 +1001,7 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     const int64_t g = pos * G / period;
     const int64_t next = std::min<int64_t>(period, ceil_div((g + 1) * period, G));  // first position of gate g+1
     const int64_t t1 = std::min<int64_t>(T, t + (next - pos));
-    segs.push_back({static_cast<int32_t>(t), static_cast<int32_t>(t1), static_cast<int32_t>(g)});
+    if (!arith) segs.push_back({static_cast<int32_t>(t), static_cast<int32_t>(t1), static_cast<int32_t>(g)});
     per_gate[g] += t1 - t;
     t = t1;
     if (static_cast<int64_t>(segs.size()) >= kMaxBatchFrames)  // (one descriptor is kept for padding)
@@ -723,9 +1017,10 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     if ((rc = order_after_last(gates[g], st))) return rc;
   const uint8_t* frame;
   int32_t np;
-  if ((rc = stage_if_needed(h0, in, T, st, &frame, &np))) return rc;
+  int64_t row_bytes;
+  if ((rc = stage_if_needed(h0, in, T, st, &frame, &np, &row_bytes))) return rc;
   CUtensorMap map;
-  if ((rc = make_tmap(&map, frame, np, h0->F, T))) return rc;
+  if ((rc = make_tmap(&map, frame, np, h0->F, T, xe::kTile, xe::kTC, row_bytes))) return rc;
   // Each (band, tile, gate) group is written once, by one CTA, with every
   // sample of its gate in this frame: stored into a fresh gate, added into
   // one that holds sums; no atomics. A gate with no samples here stays as it is.
@@ -734,6 +1029,7 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     gate_fresh[g] = gates[g]->fresh ? 1 : 0;
     if (per_gate[g] > 0) gates[g]->fresh = false;
   }
+  if (arith) return gated_arith_launch(gates, G, map, T, period, phase, per_gate, gate_fresh, st);
   // groups: one (band, tile, gate) with all its segments in time order, run by
   // one CTA back to back ("hold" between them) and written once. Groups are
   // dealt in (band, gate, tile) order, each onto the least-loaded CTA: CTAs
@@ -815,10 +1111,10 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     d.t0 = empty ? 1 : segs[s].t0;  // t0 > T: nothing is valid
     d.atomic = 0;
   }
-  const int hybrid = chunk_hybrid_flag(h0->product);
+  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps);
   if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_gated != 1 || b.key_err != h0->d_err)
-    if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid, true))) return rc;
+    if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid, 1))) return rc;
   cudaError_t e = cudaGraphLaunch(b.exec, st);
   if (e != cudaSuccess) return fail(CORR_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
   if ((e = cudaEventRecord(b.done, st)) != cudaSuccess) return fail(CORR_ECUDA, "batch event record");
@@ -837,11 +1133,24 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
 // =================================== C ABI ===================================
 extern "C" {
 
-corr_handle_t* corr_create(int32_t N, int32_t F, int32_t T) { return create_impl(N, F, T, nullptr); }
+corr_handle_t* corr_create(int32_t N, int32_t F, int32_t T) { return create_impl(N, F, T, nullptr, F, 0); }
 
 corr_handle_t* corr_create_ex(int32_t N, int32_t F, int32_t T, int32_t* acc_dev) {
   if (!acc_dev) return fail(CORR_EINVAL, "acc_dev is NULL"), nullptr;
-  return create_impl(N, F, T, acc_dev);
+  return create_impl(N, F, T, acc_dev, F, 0);
+}
+
+corr_handle_t* corr_create_bands(int32_t N, int32_t F_in, int32_t f0, int32_t f1, int32_t T) {
+  if (f1 <= f0) return fail(CORR_EINVAL, "empty band range [%d, %d)", f0, f1), nullptr;
+  return create_impl(N, f1 - f0, T, nullptr, F_in, f0);
+}
+
+int corr_bands(const corr_handle_t* h, int32_t* F_in, int32_t* f0, int32_t* f1) {
+  if (!h) return fail(CORR_EINVAL, "NULL handle");
+  if (F_in) *F_in = h->F_in;
+  if (f0) *f0 = h->f0;
+  if (f1) *f1 = h->f0 + h->F;
+  return CORR_OK;
 }
 
 int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream) {
@@ -855,8 +1164,9 @@ int corr_accumulate(corr_handle_t* h, const uint8_t* packed_dev, void* stream) {
   if ((rc = order_after_last(h, st))) return rc;
   const uint8_t* frame;
   int32_t np;
-  if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np))) return rc;
-  if ((rc = launch_frame(h, frame, np, h->plan, st))) return rc;
+  int64_t row_bytes;
+  if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np, &row_bytes))) return rc;
+  if ((rc = launch_frame(h, frame, np, row_bytes, h->plan, st))) return rc;
   h->samples += h->T;
   return record_last(h, st);
 }
@@ -870,7 +1180,8 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
                 CORR_MAX_SAMPLES);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int32_t Np = static_cast<int32_t>(ceil_div(h->N, 16) * 16);
-  const size_t row = static_cast<size_t>(h->F) * h->N;  // bytes per time sample (host layout)
+  const size_t row = static_cast<size_t>(h->F_in) * h->N;  // bytes per time sample (host layout)
+  const size_t band0 = static_cast<size_t>(h->f0) * h->N;  // the handle's first band within a time sample
   if (!h->s_copy) {
     // chunk of about T/2 samples (a stage multiple), at most 1 GiB per buffer:
     // with copies overlapping the previous frame, the correlation is the
@@ -911,17 +1222,30 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
     // buffer b's last reader: chunk c - 2 of this call, or the last chunk on b
     // of an earlier call (an event never recorded is passed at once)
     XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_used[b], 0));
-    if (Np == h->N) {
-      XE_CHECK(h, cudaMemcpyAsync(h->hchunk[b], packed_host + static_cast<size_t>(t0) * row,
-                                  static_cast<size_t>(cT) * row, cudaMemcpyHostToDevice, h->s_copy));
-    } else {
-      XE_CHECK(h, cudaMemcpy2DAsync(h->hchunk[b], Np, packed_host + static_cast<size_t>(t0) * row, h->N, h->N,
-                                    static_cast<size_t>(cT) * h->F, cudaMemcpyHostToDevice, h->s_copy));
+    // into the chunk buffer [cT][F][Np]: the handle's bands of each time sample
+    const uint8_t* src = packed_host + static_cast<size_t>(t0) * row + band0;
+    const size_t wide = static_cast<size_t>(h->F) * h->N;  // the handle's bytes per time sample
+    if (Np == h->N && h->F == h->F_in) {
+      XE_CHECK(h, cudaMemcpyAsync(h->hchunk[b], src, static_cast<size_t>(cT) * row, cudaMemcpyHostToDevice,
+                                  h->s_copy));
+    } else if (Np == h->N) {  // a band range: one row of F*N bytes per time sample
+      XE_CHECK(h, cudaMemcpy2DAsync(h->hchunk[b], wide, src, row, wide, static_cast<size_t>(cT),
+                                    cudaMemcpyHostToDevice, h->s_copy));
+    } else if (h->F == h->F_in) {  // rows of N bytes into rows of Np
+      XE_CHECK(h, cudaMemcpy2DAsync(h->hchunk[b], Np, src, h->N, h->N, static_cast<size_t>(cT) * h->F,
+                                    cudaMemcpyHostToDevice, h->s_copy));
+    } else {  // both: one 2-D copy per band
+      for (int32_t f = 0; f < h->F; ++f)
+        XE_CHECK(h, cudaMemcpy2DAsync(h->hchunk[b] + static_cast<size_t>(f) * Np, static_cast<size_t>(h->F) * Np,
+                                      src + static_cast<size_t>(f) * h->N, row, h->N, static_cast<size_t>(cT),
+                                      cudaMemcpyHostToDevice, h->s_copy));
     }
     XE_CHECK(h, cudaEventRecord(h->ev_copied[b], h->s_copy));
     XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_copied[b], 0));
     const bool tail = cT != h->hchunk_T;
-    if ((rc = launch_frame(h, h->hchunk[b], Np, tail ? h->plan_tail : h->plan_chunk, h->s_comp))) return rc;
+    if ((rc = launch_frame(h, h->hchunk[b], Np, static_cast<int64_t>(Np) * h->F, tail ? h->plan_tail : h->plan_chunk,
+                           h->s_comp)))
+      return rc;
     XE_CHECK(h, cudaEventRecord(h->ev_used[b], h->s_comp));
   }
   // the caller's stream continues after the last chunk
@@ -1074,15 +1398,21 @@ int corr_set_option(corr_handle_t* h, int option, int64_t value) {
     h->product = static_cast<int>(value);
     return CORR_OK;
   }
+  if (option == CORR_OPT_MMA_STEPS) {
+    if (value < 4 || value > 8) return fail(CORR_EINVAL, "CORR_OPT_MMA_STEPS must be in [4, 8]");
+    h->mma_steps = static_cast<int>(value);
+    return CORR_OK;
+  }
   if (option == CORR_OPT_SPLIT) {
     if (value < 0 || value > 4096) return fail(CORR_EINVAL, "CORR_OPT_SPLIT must be in [0, 4096]");
     if (h->split_opt == value) return CORR_OK;
-    h->split_opt = static_cast<int>(value);
-    // rebuild the frame schedule (after the handle's queued work has read the old one)
+    // the schedule is rebuilt, so the handle's queued work must be done reading the old one
     if (h->has_last) {
-      cudaError_t e = cudaEventSynchronize(h->last);
-      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+      cudaError_t e = cudaEventQuery(h->last);
+      if (e == cudaErrorNotReady) return fail(CORR_EBUSY, "CORR_OPT_SPLIT: the handle still has work in flight");
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventQuery");
     }
+    h->split_opt = static_cast<int>(value);
     free_plan(&h->plan);
     if ((rc = build_plan(h, h->T, &h->plan))) return rc;
     if (h->plan_chunk.d_items) {
@@ -1102,6 +1432,7 @@ int64_t corr_get_option(const corr_handle_t* h, int option) {
   if (!h) return fail(CORR_EINVAL, "NULL handle");
   if (option == CORR_OPT_PRODUCT) return effective_product(h->product);
   if (option == CORR_OPT_SPLIT) return h->split_opt;
+  if (option == CORR_OPT_MMA_STEPS) return h->mma_steps;
   return fail(CORR_EINVAL, "unknown option %d", option);
 }
 
@@ -1128,9 +1459,19 @@ int corr_synchronize(corr_handle_t* h, int64_t timeout_ms) {
 int corr_status(corr_handle_t* h) {
   if (!h) return fail(CORR_EINVAL, "NULL handle");
   if (h->sticky != CORR_OK) return h->sticky;
-  int32_t err = 0;
-  cudaError_t e = cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(h, e, "reading device error word");
+  if (!h->s_status) {
+    XE_CHECK(h, cudaStreamCreateWithFlags(&h->s_status, cudaStreamNonBlocking));
+    cudaError_t ae = cudaHostAlloc(reinterpret_cast<void**>(&h->h_status), sizeof(int32_t), cudaHostAllocDefault);
+    if (ae != cudaSuccess) {
+      h->h_status = nullptr;
+      return alloc_failed("status word", sizeof(int32_t), ae);
+    }
+  }
+  // the fault word as it stands after the handle's last call (other streams' work is not waited for)
+  if (h->has_last) XE_CHECK(h, cudaStreamWaitEvent(h->s_status, h->last, 0));
+  XE_CHECK(h, cudaMemcpyAsync(h->h_status, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s_status));
+  XE_CHECK(h, cudaStreamSynchronize(h->s_status));
+  const int32_t err = *h->h_status;
   if (err) {
     h->sticky = CORR_ETIMEOUT;
     return fail(CORR_ETIMEOUT, "device reported a wait that ran out (code %d)", err);
@@ -1168,6 +1509,8 @@ void corr_destroy(corr_handle_t* h) {
     if (h->ev_used[k]) cudaEventDestroy(h->ev_used[k]);
   }
   if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->s_status) cudaStreamDestroy(h->s_status);
+  if (h->h_status) cudaFreeHost(h->h_status);
   if (h->s_copy) cudaStreamDestroy(h->s_copy);
   if (h->s_comp) cudaStreamDestroy(h->s_comp);
   if (h->last) cudaEventDestroy(h->last);
@@ -1213,14 +1556,15 @@ double corr_effective_ops(int32_t N, int32_t F, int32_t T) {
 // Allocation-free correlation of one frame (corr_correlate_noalloc).
 //
 // Some callers cannot allocate device memory when they need a correlation:
-// code that runs while a stream is being captured into a CUDA graph (where
-// cudaMalloc and cudaFree are not allowed), applications whose device memory
-// belongs to their own pool allocator and may not be taken behind its back,
-// and real-time hosts that reserve every byte up front and forbid allocations
-// on the processing path. corr_correlate_noalloc serves them: the caller
-// passes the frame and the output buffer, and the only other device memory the
-// kernel needs (its work list and its fault word) is the fixed array below.
-// Every GPU that loads this library holds that array until the process exits.
+// applications whose device memory belongs to their own pool allocator and
+// may not be taken behind its back, and real-time hosts that reserve every
+// byte up front and forbid allocations on the processing path.
+// corr_correlate_noalloc serves them: the caller passes the frame and the
+// output buffer, and the only other device memory the kernel needs (its work
+// list and its fault word) is the fixed array below. Every GPU that loads
+// this library holds that array until the process exits. Its device address
+// is looked up once per device and kept, so a cudaDeviceReset while the
+// library is in use is not supported.
 // =============================================================================
 namespace {
 

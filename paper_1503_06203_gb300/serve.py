@@ -12,9 +12,10 @@ memory budget (first-fit blocks inside one preallocated slab), copies each admit
 frame to the device on a copy stream, and launches every copied frame not
 yet correlated in one batched launch (at most one frame per stream per
 launch: a stream's frames add into the same accumulators in arrival
-order). Frames keep arriving and copying while launches run; up to two
-launches are in flight. The plain mode is the reference: one frame per
-launch, each waited for before the next starts.
+order). Frames keep arriving and copying while launches run; up to three
+launches are in flight (the library keeps four launch sets, so the host
+never waits for the GPU to launch). The plain mode is the reference: one
+frame per launch, each waited for before the next starts.
 
 PyTorch provides device memory, pinned host memory and streams; every
 correlation runs in the CUDA library.
@@ -49,8 +50,12 @@ class Arrival:
 
 @dataclass
 class FrameRecord:
+    """Host-clock times (seconds after the start of the run) of one frame's steps."""
     arrival: float
-    done: float = float("nan")
+    admitted: float = float("nan")   # input space granted, copy issued
+    copied: float = float("nan")     # copy seen complete
+    launched: float = float("nan")   # in a launch
+    done: float = float("nan")       # its launch seen complete
 
 
 @dataclass
@@ -60,14 +65,30 @@ class RunStats:
     seconds: float
     latencies_ms: list = field(default_factory=list)
     ops: float = 0.0
+    records: list = field(default_factory=list)  # FrameRecord per frame (served mode)
+    launches: int = 0
+
+    def breakdown(self) -> dict:
+        """p50 / p99 of each step's share of the latency (served mode), in ms."""
+        if not self.records:
+            return {}
+        r = self.records
+        parts = {"wait_for_space": [x.admitted - x.arrival for x in r], "copy": [x.copied - x.admitted for x in r],
+                 "wait_for_launch": [x.launched - x.copied for x in r], "gpu": [x.done - x.launched for x in r]}
+        return {k: {"p50": round(1e3 * float(np.percentile(v, 50)), 3), "p99": round(1e3 * float(np.percentile(v, 99)), 3)}
+                for k, v in parts.items()}
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms)
-        return {"mode": self.mode, "frames": self.frames, "seconds": round(self.seconds, 4),
-                "frames_per_s": round(self.frames / self.seconds, 3),
-                "effective_tops": round(self.ops / self.seconds / 1e12, 3),
-                "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat.size else None,
-                "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat.size else None}
+        out = {"mode": self.mode, "frames": self.frames, "seconds": round(self.seconds, 4),
+               "frames_per_s": round(self.frames / self.seconds, 3),
+               "effective_tops": round(self.ops / self.seconds / 1e12, 3),
+               "p50_ms": round(float(np.percentile(lat, 50)), 3) if lat.size else None,
+               "p99_ms": round(float(np.percentile(lat, 99)), 3) if lat.size else None,
+               "launches": self.launches}
+        if self.records:
+            out["latency_parts_ms"] = self.breakdown()
+        return out
 
 
 def poisson_arrivals(rate_hz: float, count: int, streams: int, t_min: int, t_max: int, pool_bytes: int,
@@ -163,6 +184,13 @@ class Server:
                 with torch.cuda.stream(self.compute_stream):
                     self.readouts[stream_id].append(self.outs[stream_id].cpu())
 
+    def close(self):
+        for c in self.cors:
+            c.close()
+        self.cors = []
+        self.outs = []
+        self.ring.buf = None
+
     def reset(self):
         for c in self.cors:
             c.reset()
@@ -174,7 +202,7 @@ class Server:
                    for a in arrivals)
 
     # ---------------------------------------------------------------- served
-    def run_served(self, arrivals: list[Arrival], max_inflight: int = 2) -> RunStats:
+    def run_served(self, arrivals: list[Arrival], max_inflight: int = 3) -> RunStats:
         recs = [FrameRecord(a.t) for a in arrivals]
         pending = collections.deque(range(len(arrivals)))  # not yet arrived
         waiting = collections.deque()   # arrived, waiting for budget
@@ -184,6 +212,7 @@ class Server:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         done = 0
+        launches = 0
         while done < len(arrivals):
             now = time.perf_counter() - t0
             while pending and arrivals[pending[0]].t <= now:
@@ -197,6 +226,7 @@ class Server:
                 if off is None:
                     break
                 waiting.popleft()
+                recs[k].admitted = time.perf_counter() - t0
                 src = self._frame_view(a)
                 dst = self.ring.buf[off:off + src.numel()]
                 with torch.cuda.stream(self.copy_stream):
@@ -206,6 +236,7 @@ class Server:
                 copying.append((k, off, ev))
             while copying and copying[0][2].query():
                 k, off, _ = copying.popleft()
+                recs[k].copied = time.perf_counter() - t0
                 ready.append((k, off))
             # one launch over every copied frame, one frame per stream (oldest first)
             if ready and len(inflight) < max_inflight:
@@ -225,7 +256,10 @@ class Server:
                     cors.append(self.cors[a.stream])
                     xs.append(self.ring.buf[off:off + a.T * s.F * s.N].view(a.T, s.F, s.N))
                 accumulate_batch(cors, xs, stream=self.compute_stream)
+                launches += 1
+                t_launch = time.perf_counter() - t0
                 for k, _ in chosen:
+                    recs[k].launched = t_launch
                     self._after_frame(arrivals[k].stream)
                 ev = torch.cuda.Event()
                 ev.record(self.compute_stream)
@@ -240,9 +274,8 @@ class Server:
             if not (inflight and inflight[0][0].query()) and not copying and not ready:
                 time.sleep(20e-6)
         seconds = time.perf_counter() - t0 - arrivals[0].t
-        st = RunStats("served", len(arrivals), seconds, [1e3 * (r.done - a.t) for r, a in zip(recs, arrivals)],
-                      self.ops(arrivals))
-        return st
+        return RunStats("served", len(arrivals), seconds, [1e3 * (r.done - a.t) for r, a in zip(recs, arrivals)],
+                        self.ops(arrivals), recs, launches)
 
     # ---------------------------------------------------------------- plain
     def run_plain(self, arrivals: list[Arrival]) -> RunStats:
@@ -263,4 +296,4 @@ class Server:
             self.compute_stream.synchronize()
             lat.append(1e3 * (time.perf_counter() - t0 - a.t))
         seconds = time.perf_counter() - t0 - arrivals[0].t
-        return RunStats("plain", len(arrivals), seconds, lat, self.ops(arrivals))
+        return RunStats("plain", len(arrivals), seconds, lat, self.ops(arrivals), launches=len(arrivals))

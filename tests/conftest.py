@@ -76,3 +76,25 @@ def read_paper_numbers():
                 k, v = line.split()[:2]
                 vals[k] = float(v)
     return vals
+
+
+def freivalds_rows(V, w):
+    """(V w) per band for packed visibilities V int [F][N(N+1)/2][2] and complex weights w int64 [F][N][2],
+    V extended to the full matrix by Hermitian symmetry. Exact: every partial sum is an integer below 2^53.
+    Returns int64 [F][N][2]."""
+    import numpy as np
+    F, B, _ = V.shape
+    N = int((np.sqrt(8 * B + 1) - 1) // 2)
+    iu, ju = np.triu_indices(N)
+    off = iu != ju
+    out = np.empty((F, N, 2), dtype=np.int64)
+    for b in range(F):
+        wc = w[b, :, 0] + 1j * w[b, :, 1]
+        Vc = V[b, :, 0].astype(np.float64) + 1j * V[b, :, 1].astype(np.float64)
+        t1 = Vc * wc[ju]                    # upper part: V_ij w_j into row i
+        t2 = np.conj(Vc[off]) * wc[iu[off]]  # lower part: conj(V_ij) w_i into row j
+        lr = np.bincount(iu, weights=t1.real, minlength=N) + np.bincount(ju[off], weights=t2.real, minlength=N)
+        li = np.bincount(iu, weights=t1.imag, minlength=N) + np.bincount(ju[off], weights=t2.imag, minlength=N)
+        out[b, :, 0] = np.rint(lr).astype(np.int64)
+        out[b, :, 1] = np.rint(li).astype(np.int64)
+    return out

@@ -11,8 +11,10 @@ def test_cache_roundtrip_and_candidates(tmp_path):
     assert autotune.load_cache(p) == {}
     autotune.save_cache({"gpu": {autotune.shape_key(256, 4, 100): {"product": 0, "split": 2}}}, p)
     assert autotune.load_cache(p)["gpu"]["N256_F4_T100"]["split"] == 2
-    assert (1, 4) in autotune.candidates(4096) and (0, 0) in autotune.candidates(4096)
-    assert all(s <= 1 for _, s in autotune.candidates(128))  # one chunk: no splits beyond 1
+    cands = autotune.candidates(4096)
+    assert cands[0] == (1, 6, 0)  # the library default is tried first
+    assert (1, 6, 4) in cands and (0, 8, 0) in cands and {m for _, m, _ in cands} == {4, 5, 6, 7, 8}
+    assert all(s <= 1 for _, _, s in autotune.candidates(128))  # one chunk: no splits beyond 1
 
 
 def test_pick_keeps_default_within_margin():
@@ -38,16 +40,16 @@ def test_every_knob_is_bit_exact_and_tuning_caches(tmp_path):
     ref = oracle.visibilities(x)
     xd = torch.from_numpy(x).cuda()
     with xe.Correlator(N, F, T) as c:
-        for product, split in autotune.candidates(T):
-            c.set_option(xe.CORR_OPT_PRODUCT, product)
-            c.set_option(xe.CORR_OPT_SPLIT, split)
-            assert c.get_option(xe.CORR_OPT_PRODUCT) == product
+        for product, mma_steps, split in autotune.candidates(T):  # every structural candidate, bit-exact
+            autotune.set_knobs(c, product, mma_steps, split)
+            assert c.get_option(xe.CORR_OPT_PRODUCT) == product and c.get_option(xe.CORR_OPT_MMA_STEPS) == mma_steps
             c.reset()
             c.accumulate(xd)
-            assert np.array_equal(c.readout().cpu().numpy().astype(np.int64), ref), (product, split)
+            assert np.array_equal(c.readout().cpu().numpy().astype(np.int64), ref), (product, mma_steps, split)
     p = str(tmp_path / "tune.json")
     e = autotune.tune(N, F, T, reps=2, path=p)
-    assert (e["product"], e["split"]) in autotune.candidates(T) and len(e["trials"]) == len(autotune.candidates(T))
+    assert (e["product"], e["mma_steps"], e["split"]) in autotune.candidates(T)
+    assert len(e["trials"]) == len(autotune.candidates(T))
     with xe.Correlator(N, F, T) as c:
         assert autotune.apply(c, path=p, tune_if_missing=False)["ms"] == e["ms"]
         assert c.get_option(xe.CORR_OPT_PRODUCT) == e["product"]

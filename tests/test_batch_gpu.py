@@ -117,3 +117,26 @@ def test_full_uneven_batch_sampled_and_freivalds(xe):
             li = np.bincount(iu, weights=t1.imag, minlength=fr.N) + np.bincount(ju[off], weights=t2.imag, minlength=fr.N)
             assert np.array_equal(np.rint(lr).astype(np.int64), rhs[b, :, 0]), (k, b)
             assert np.array_equal(np.rint(li).astype(np.int64), rhs[b, :, 1]), (k, b)
+
+
+def test_batch_time_split_and_ring_reuse(xe):
+    """A lone frame with few tiles and a long time axis is cut into time ranges (atomic adds onto
+    zeroed, then onto resident sums); ten launches of changing sizes cycle through every launch set."""
+    import torch
+    N, F, T = 64, 1, 8192  # one tile, 64 chunks: split across many CTAs
+    c = xe.Correlator(N, F, T)
+    xs = [synth.gauss(N, F, T, 2.5, 600 + k) for k in range(2)]
+    for x in xs:
+        xe.accumulate_batch([c], [torch.from_numpy(x).cuda()])
+    assert np.array_equal(c.readout(reset=True).cpu().numpy().astype(np.int64),
+                          oracle.visibilities(xs[0]) + oracle.visibilities(xs[1]))
+    frames = small_batch(10, 31)
+    cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
+    for k in range(10):
+        sub = list(range(k % 5, len(frames), 1 + k % 3))
+        xk = [synth.gauss(frames[i].N, frames[i].F, frames[i].T, 2.5, 700 + 10 * k + i) for i in sub]
+        xe.accumulate_batch([cors[i] for i in sub], [torch.from_numpy(x).cuda() for x in xk])
+        for i, x in zip(sub, xk):
+            assert np.array_equal(cors[i].readout(reset=True).cpu().numpy().astype(np.int64),
+                                  oracle.visibilities(x)), (k, i)
+    torch.cuda.synchronize()

@@ -20,6 +20,13 @@ def xe():
     (96, 3, 1000, 3, 100, 37),     # edges inside chunks, ragged end
     (17, 1, 777, 5, 777, 5),       # one period, unaligned rows (staging)
     (256, 2, 4096, 8, 512, 300),
+    # periods of a chunk or more run the gate-arithmetic kernel: every chunk meets its gate in two runs,
+    # gates of many chunks, a frame shorter than a period (gates without samples), many gates
+    (64, 2, 1024, 2, 128, 50),
+    (128, 1, 5000, 8, 16384, 1000),
+    (64, 3, 300, 4, 1024, 900),
+    (96, 1, 3000, 7, 1000, 999),
+    (64, 1, 4096, 64, 4096, 17),
 ])
 def test_gated_matches_oracle(xe, N, F, T, G, period, phase):
     import torch

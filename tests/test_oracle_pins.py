@@ -55,13 +55,15 @@ def test_all_byte_pairs_brute_force():
     a, b = np.meshgrid(vals, vals, indexing="ij")
     x = np.stack([a.ravel(), b.ravel()], axis=1).reshape(1, -1, 2).astype(np.uint8)  # T=1, F=65536, N=2
     V = oracle.visibilities(np.ascontiguousarray(x))
-    for k in range(0, 65536, 97):  # a spread sample through all pairs
-        X = complex((int(a.ravel()[k]) >> 4) - 8, (int(a.ravel()[k]) & 15) - 8)
-        Y = complex((int(b.ravel()[k]) >> 4) - 8, (int(b.ravel()[k]) & 15) - 8)
+    # each byte decoded once with Python integers: value = nibble - 8, high nibble real
+    dec = [complex((v >> 4) - 8, (v & 15) - 8) for v in range(256)]
+    A, Bv = a.ravel(), b.ravel()
+    for k in range(65536):  # every one of the 256 x 256 byte pairs
+        X, Y = dec[int(A[k])], dec[int(Bv[k])]
         z = X * Y.conjugate()
-        assert tuple(V[k, 1]) == (int(z.real), int(z.imag))
-        assert tuple(V[k, 0]) == (int((X * X.conjugate()).real), 0)
-        assert tuple(V[k, 2]) == (int((Y * Y.conjugate()).real), 0)
+        assert (int(V[k, 1, 0]), int(V[k, 1, 1])) == (int(z.real), int(z.imag)), k
+        assert (int(V[k, 0, 0]), int(V[k, 0, 1])) == (int((X * X.conjugate()).real), 0), k
+        assert (int(V[k, 2, 0]), int(V[k, 2, 1])) == (int((Y * Y.conjugate()).real), 0), k
 
 
 @pytest.mark.parametrize("N,F,T,seed", [(1, 1, 1, 1), (3, 2, 5, 2), (8, 3, 16, 3), (5, 1, 13, 4)])
@@ -275,3 +277,11 @@ def test_gated_pulse_closed_form():
     qr, qi = (q[on] >> 4).astype(np.int64) - 8, (q[on] & 15).astype(np.int64) - 8
     assert (V[0, :, :, 0] == int((qr * qr + qi * qi).sum())).all() and not V[0, :, :, 1].any()
     assert not V[1:].any()
+
+
+def test_freivalds_rows_helper():
+    """The test helper that forms V w from a packed triangle (Hermitian extension) against the oracle's rhs."""
+    from conftest import freivalds_rows
+    x = synth.gauss(70, 3, 150, 2.5, 25)
+    w = np.random.default_rng(2).integers(-3, 4, size=(3, 70, 2)).astype(np.int64)
+    assert np.array_equal(freivalds_rows(oracle.visibilities(x), w), oracle.freivalds_rhs(x, w))
