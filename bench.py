@@ -311,6 +311,29 @@ def measure_peaks(L, sp) -> dict:
     return {"imma": imma, "combo": combo, "dp4a": dp4a, "int_mm": int_mm_rate()}
 
 
+def pinned_copy(x_np):
+    """A pinned host copy of a numpy array, read once by the GPU before any timing.
+
+    The generator writes ordinary memory (byte-by-byte writes straight into pinned
+    memory were measured at tens of MB/s on this machine's Grace hosts), and the copy into
+    pinned memory is one bulk numpy copy. On these hosts the GPU's first read of
+    host pages the CPU has just written runs at 3-20 GB/s and later reads at about
+    210 GB/s, so one untimed pass gives every timed copy the steady rate.
+    """
+    import torch
+    t = torch.empty(x_np.shape, dtype=torch.uint8).pin_memory()
+    t.numpy()[...] = x_np
+    flat = t.view(-1)
+    step = 1 << 30
+    buf = torch.empty(min(step, flat.numel()), dtype=torch.uint8, device="cuda")
+    for k in range(0, flat.numel(), step):
+        n = min(step, flat.numel() - k)
+        buf[:n].copy_(flat[k:k + n], non_blocking=True)
+    torch.cuda.synchronize()
+    del buf
+    return t
+
+
 def h2d_rate(x_host, x_dev) -> float:
     """This machine's host-to-device copy rate from pinned memory, GB/s (context for the e2e figure)."""
     import torch
@@ -348,8 +371,7 @@ def single_frame_record(args, wl_key, frame, peaks, rank=0, world=1, bands=None,
     in_bytes = N * Fb * T
     out_bytes = Fb * xe.baselines(N) * 2 * 4
     stream = torch.cuda.current_stream()
-    x_host = torch.empty((T, F, N), dtype=torch.uint8).pin_memory()
-    frame.make(out=x_host.numpy())
+    x_host = pinned_copy(frame.make())
     x_dev = torch.empty((T, F, N), dtype=torch.uint8, device="cuda")
     h2d_gbs = h2d_rate(x_host, x_dev)
 
@@ -625,8 +647,7 @@ def served_record(args) -> dict:
     specs = served_specs()
     t_min, t_max = 1024, 8192
     pool_bytes = max(s.N * s.F for s in specs) * t_max
-    pool = torch.empty(pool_bytes, dtype=torch.uint8).pin_memory()
-    synth.gauss(pool_bytes, 1, 1, 2.5, 1004, out=pool.numpy().reshape(1, 1, -1))
+    pool = pinned_copy(synth.gauss(pool_bytes, 1, 1, 2.5, 1004).reshape(-1))
     budget = 24 << 30
     srv = serve.Server(specs, t_max, pool, budget_bytes=budget, readout_every=16)
     sweeps = []

@@ -893,7 +893,7 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
 // fresh flag, the gate arithmetic), one item per (band, tile, gate) over the
 // whole frame; the kernel visits only the chunks that hold samples of the
 // item's gate and masks the other rows. Items are dealt round-robin in
-// (band, gate, tile) order, so CTAs running together share a band's input.
+// (gate, band, tile) order.
 int gated_arith_launch(corr_handle_t* const* gates, int G, const CUtensorMap& map, int32_t T, int32_t period,
                        int32_t phase, const std::vector<int64_t>& per_gate, const std::vector<int32_t>& gate_fresh,
                        cudaStream_t st) {
@@ -923,13 +923,16 @@ int gated_arith_launch(corr_handle_t* const* gates, int G, const CUtensorMap& ma
   }
   int rc = grow_set(b, static_cast<size_t>(G), static_cast<size_t>(nitems));
   if (rc) return rc;
+  // gate-major: a CTA's consecutive items (grid apart) mostly share a gate, so
+  // its descriptor rarely changes; the CTAs running together still take the
+  // tiles of a few bands of one gate and share those bands' input in L2
   int64_t k = 0;
-  for (int32_t f = 0; f < h0->F; ++f)
-    for (int g = 0; g < G; ++g) {
-      if (per_gate[g] == 0) continue;
+  for (int g = 0; g < G; ++g) {
+    if (per_gate[g] == 0) continue;
+    for (int32_t f = 0; f < h0->F; ++f)
       for (size_t u = 0; u < bi.size(); ++u)
         b.h_items[k++] = make_int4(f | (g << 20), bi[u] | (bj[u] << 16), 0, nch);
-    }
+  }
   for (int g = 0; g < G; ++g) {
     xe::FrameDesc& d = b.h_desc[g];
     d.map = map;

@@ -167,6 +167,7 @@ class Server:
         self.keep_readouts = False
         self.counts = [0] * len(specs)
         self.ring = SlabAllocator(budget_bytes)
+        self.rate_tops = 200.0  # effective TOPS assumed when estimating a frame's GPU time
         self.copy_stream = torch.cuda.Stream()
         self.compute_stream = torch.cuda.Stream()
 
@@ -202,7 +203,12 @@ class Server:
                    for a in arrivals)
 
     # ---------------------------------------------------------------- served
-    def run_served(self, arrivals: list[Arrival], max_inflight: int = 3) -> RunStats:
+    def frame_ms(self, a: Arrival) -> float:
+        """Estimated GPU time of a frame: its Eq. 2 operations at rate_tops."""
+        s = self.specs[a.stream]
+        return 4.0 * s.N * (s.N + 1) * s.F * a.T / (self.rate_tops * 1e9)
+
+    def run_served(self, arrivals: list[Arrival], max_inflight: int = 3, small_ms: float = 2.0) -> RunStats:
         recs = [FrameRecord(a.t) for a in arrivals]
         pending = collections.deque(range(len(arrivals)))  # not yet arrived
         waiting = collections.deque()   # arrived, waiting for budget
@@ -238,16 +244,21 @@ class Server:
                 k, off, _ = copying.popleft()
                 recs[k].copied = time.perf_counter() - t0
                 ready.append((k, off))
-            # one launch over every copied frame, one frame per stream (oldest first)
+            # one launch over copied frames in arrival order, one frame per stream; a frame whose work
+            # is more than the launch's so far (and more than small_ms) starts the next launch instead,
+            # so older frames never wait for a larger, younger one (all frames of a launch finish together)
             if ready and len(inflight) < max_inflight:
-                chosen, seen, rest = [], set(), []
+                chosen, seen, rest, work, cut = [], set(), [], 0.0, False
                 for k, off in ready:
-                    sid = arrivals[k].stream
-                    if sid in seen:
+                    a = arrivals[k]
+                    w = self.frame_ms(a)
+                    if cut or a.stream in seen or (chosen and w > max(work, small_ms)):
+                        cut = cut or a.stream not in seen
                         rest.append((k, off))
                     else:
-                        seen.add(sid)
+                        seen.add(a.stream)
                         chosen.append((k, off))
+                        work += w
                 ready = rest
                 cors, xs = [], []
                 for k, off in chosen:
