@@ -137,6 +137,24 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
 int corr_readout(corr_handle_t* h, int32_t* vis_dev, int reset, void* stream);
 int corr_readout_host(corr_handle_t* h, int32_t* vis_host, int reset, void* stream);
 
+/*
+ * corr_readout_async / corr_readout_host_async -- end the integration and
+ * copy its visibilities int32 V[F][B][2] to vis (device or host memory),
+ * overlapped with the next integration (Sec. II.A: visibilities are read out
+ * once an integration ends, while the next one accumulates). The handle keeps
+ * a second accumulator set (allocated on the first call, F*B(N)*2 int32 in
+ * device memory, freed by corr_destroy): the finished set is copied out on
+ * copy_stream, after the handle's last call, while the handle's later calls
+ * add into the other set, starting from zero. The copy is ordered on
+ * copy_stream only, not on the handle's other streams: synchronise
+ * copy_stream (or make a stream wait on it) before reading vis. The next
+ * write into a set waits, on the device, for that set's last copy out, so
+ * readouts may alternate freely with accumulates. Like corr_readout with
+ * reset != 0 otherwise. CORR_ENOMEM if the second set cannot be allocated.
+ */
+int corr_readout_async(corr_handle_t* h, int32_t* vis_dev, void* copy_stream);
+int corr_readout_host_async(corr_handle_t* h, int32_t* vis_host, void* copy_stream);
+
 /* corr_reset -- return the accumulators to the all-zero state without a readout. */
 int corr_reset(corr_handle_t* h, void* stream);
 

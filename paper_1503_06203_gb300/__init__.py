@@ -166,6 +166,16 @@ class Correlator:
         check(lib().corr_readout_host(self._h, ctypes.c_void_p(ptr), int(reset), _stream_ptr(stream)))
         return out
 
+    def readout_async(self, out, copy_stream):
+        """End the integration; copy it into `out` (CUDA or host int32 [F][N(N+1)/2][2]) on copy_stream,
+        overlapped with the next integration (a second accumulator set). Synchronise copy_stream before
+        reading `out`."""
+        import torch
+        assert out.dtype == torch.int32 and out.is_contiguous() and out.numel() == self.F * baselines(self.N) * 2
+        fn = lib().corr_readout_async if out.is_cuda else lib().corr_readout_host_async
+        check(fn(self._h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(copy_stream)))
+        return out
+
     def reset(self, stream=None):
         check(lib().corr_reset(self._h, _stream_ptr(stream)))
 

@@ -31,6 +31,8 @@ SIGNATURES = [
     ("corr_accumulate_host", _int, [_vp, _vp, _vp]),
     ("corr_readout", _int, [_vp, _vp, _int, _vp]),
     ("corr_readout_host", _int, [_vp, _vp, _int, _vp]),
+    ("corr_readout_async", _int, [_vp, _vp, _vp]),
+    ("corr_readout_host_async", _int, [_vp, _vp, _vp]),
     ("corr_reset", _int, [_vp, _vp]),
     ("corr_accumulate_batch", _int, [_vp, _vp, _int, _vp]),
     ("corr_accumulate_batch_ex", _int, [_vp, _vp, _vp, _int, _vp]),

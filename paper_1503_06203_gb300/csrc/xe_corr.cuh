@@ -361,10 +361,13 @@ __device__ __forceinline__ void write_piece(int N, int64_t B, int32_t* vis, int 
 // b = ceil((g + 1) P / G): floor(pos G / P) == g exactly there. Sample t has
 // position (t + phase) mod P. Chunks are kTC samples; P >= kTC, so a chunk's
 // positions wrap at most once and the gate meets a chunk in at most two runs.
+// 32-bit unsigned arithmetic is exact: sample indices are below 2^31 and the
+// host takes this route only for P <= 2^29, so sample + phase and
+// sample + 2P stay below 2^32.
 
 // The first sample >= s whose position lies in [a, b) (a < b <= P).
-__device__ __forceinline__ int64_t gate_next_sample(int64_t s, int32_t P, int32_t phase, int32_t a, int32_t b) {
-  const int32_t pos = static_cast<int32_t>((s + phase) % P);
+__device__ __forceinline__ uint32_t gate_next_sample(uint32_t s, uint32_t P, uint32_t phase, uint32_t a, uint32_t b) {
+  const uint32_t pos = (s + phase) % P;
   if (pos >= a && pos < b) return s;
   return s + (pos < a ? a - pos : P - pos + a);
 }
@@ -373,8 +376,9 @@ __device__ __forceinline__ int64_t gate_next_sample(int64_t s, int32_t P, int32_
 __device__ __forceinline__ int32_t gate_chunk(int32_t c, int32_t nch, int32_t T, int32_t P, int32_t phase, int32_t a,
                                               int32_t b) {
   if (c >= nch || a >= b) return nch;
-  const int64_t s = gate_next_sample(static_cast<int64_t>(c) * kTC, P, phase, a, b);
-  return s >= T ? nch : static_cast<int32_t>(s / kTC);
+  const uint32_t s = gate_next_sample(static_cast<uint32_t>(c) * kTC, static_cast<uint32_t>(P),
+                                      static_cast<uint32_t>(phase), static_cast<uint32_t>(a), static_cast<uint32_t>(b));
+  return s >= static_cast<uint32_t>(T) ? nch : static_cast<int32_t>(s / kTC);
 }
 
 // The gate's rows of chunk c (relative to its first sample), as two windows
@@ -382,9 +386,9 @@ __device__ __forceinline__ int32_t gate_chunk(int32_t c, int32_t nch, int32_t T,
 // and the run after it; both clipped to the frame's T samples.
 __device__ __forceinline__ void gate_windows(int32_t c, int32_t T, int32_t P, int32_t phase, int32_t a, int32_t b,
                                              ChunkMeta& m) {
-  const int64_t s0 = static_cast<int64_t>(c) * kTC;
-  const int32_t p0 = static_cast<int32_t>((s0 + phase) % P);
-  const int32_t tmax = static_cast<int32_t>(min(static_cast<int64_t>(kTC), static_cast<int64_t>(T) - s0));
+  const uint32_t s0 = static_cast<uint32_t>(c) * kTC;
+  const int32_t p0 = static_cast<int32_t>((s0 + static_cast<uint32_t>(phase)) % static_cast<uint32_t>(P));
+  const int32_t tmax = min(kTC, T - static_cast<int32_t>(s0));
   m.lo = max(0, a - p0);
   m.hi = min(tmax, b - p0);
   m.lo2 = max(0, a - p0 + P);

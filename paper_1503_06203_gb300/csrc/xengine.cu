@@ -178,6 +178,14 @@ struct corr_handle {
   // after the handle's last call only (not after unrelated work)
   cudaStream_t s_status = nullptr;
   int32_t* h_status = nullptr;
+  // overlapped readouts (corr_readout_async): a second accumulator set; the
+  // event after the copy out of each set; whether the active set must wait
+  // for its copy out before the next write into it
+  int32_t* acc_alt = nullptr;
+  cudaEvent_t ev_copied_out[2] = {nullptr, nullptr};
+  int active_set = 0;         // which of {the handle's own set, acc_alt} is acc (0: acc_own)
+  int32_t* acc_own = nullptr; // the set the handle was created with
+  bool acc_wait = false;      // the active set still has a copy out in flight
 };
 
 namespace {
@@ -316,9 +324,15 @@ int make_tmap(CUtensorMap* m, const uint8_t* base, int32_t Np, int32_t F, int32_
   return CORR_OK;
 }
 
-// Order this call after the handle's previous call if that ran on another stream.
+// Order this call after the handle's previous call if that ran on another
+// stream, and after the copy out of the active accumulator set if an
+// overlapped readout of that set is still in flight.
 int order_after_last(corr_handle* h, cudaStream_t st) {
   if (h->has_last && h->last_stream != st) XE_CHECK(h, cudaStreamWaitEvent(st, h->last, 0));
+  if (h->acc_wait) {
+    XE_CHECK(h, cudaStreamWaitEvent(st, h->ev_copied_out[h->active_set], 0));
+    h->acc_wait = false;
+  }
   return CORR_OK;
 }
 
@@ -1277,6 +1291,47 @@ static int readout_impl(corr_handle_t* h, int32_t* vis, int reset, void* stream,
   return record_last(h, st);
 }
 
+// Overlapped readout: the finished integration is copied out of the active
+// set on copy_stream while the handle continues in the other set.
+static int readout_async_impl(corr_handle_t* h, int32_t* vis, void* copy_stream, cudaMemcpyKind kind) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!vis) return fail(CORR_EINVAL, "output pointer is NULL");
+  cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+  const size_t bytes = static_cast<size_t>(h->F) * h->B * 2 * sizeof(int32_t);
+  if (!h->acc_alt) {
+    cudaError_t e = cudaMalloc(&h->acc_alt, bytes);
+    if (e != cudaSuccess) {
+      h->acc_alt = nullptr;
+      return alloc_failed("second accumulator set", bytes, e);
+    }
+    for (int k = 0; k < 2; ++k) XE_CHECK(h, cudaEventCreateWithFlags(&h->ev_copied_out[k], cudaEventDisableTiming));
+    h->acc_own = h->acc;
+  }
+  // the copy follows the handle's last call (and a pending copy out of this set)
+  if ((rc = order_after_last(h, cs))) return rc;
+  if (h->fresh) XE_CHECK(h, cudaMemsetAsync(h->acc, 0, bytes, cs));  // an empty integration reads as zeros
+  XE_CHECK(h, cudaMemcpyAsync(vis, h->acc, bytes, kind, cs));
+  XE_CHECK(h, cudaEventRecord(h->ev_copied_out[h->active_set], cs));
+  // continue in the other set, fresh; before its first write, wait for its own copy out, if one was made
+  const int next = h->active_set ^ 1;
+  h->acc = next ? h->acc_alt : h->acc_own;
+  h->active_set = next;
+  h->acc_wait = true;  // (an event never recorded is passed at once)
+  h->fresh = true;
+  h->samples = 0;
+  // the handle's next call orders itself after its last compute, not after this copy
+  return CORR_OK;
+}
+
+int corr_readout_async(corr_handle_t* h, int32_t* vis_dev, void* copy_stream) {
+  return readout_async_impl(h, vis_dev, copy_stream, cudaMemcpyDeviceToDevice);
+}
+
+int corr_readout_host_async(corr_handle_t* h, int32_t* vis_host, void* copy_stream) {
+  return readout_async_impl(h, vis_host, copy_stream, cudaMemcpyDeviceToHost);
+}
+
 int corr_readout(corr_handle_t* h, int32_t* vis_dev, int reset, void* stream) {
   return readout_impl(h, vis_dev, reset, stream, cudaMemcpyDeviceToDevice);
 }
@@ -1499,6 +1554,15 @@ const char* corr_last_error(void) { return g_last_error.c_str(); }
 void corr_destroy(corr_handle_t* h) {
   if (!h) return;
   if (h->has_last) cudaEventSynchronize(h->last);
+  for (int k = 0; k < 2; ++k)
+    if (h->ev_copied_out[k]) {
+      cudaEventSynchronize(h->ev_copied_out[k]);  // overlapped readouts still copying out
+      cudaEventDestroy(h->ev_copied_out[k]);
+    }
+  if (h->acc_alt) {  // both sets: free the library's, leave a caller-owned one to the caller
+    cudaFree(h->acc_alt);
+    h->acc = h->acc_own;
+  }
   if (h->own_acc && h->acc) cudaFree(h->acc);
   if (h->d_err) cudaFree(h->d_err);
   free_plan(&h->plan);

@@ -88,6 +88,19 @@ def gauss(N: int, F: int, T: int, sigma: float, seed: int, tone_amp: float = 0.0
     return out
 
 
+def gauss_flat(nbytes: int, sigma: float, seed: int, nthreads: int | None = None) -> np.ndarray:
+    """`nbytes` Gaussian-level bytes as one flat array, the same bytes as gauss(nbytes, 1, 1, ...).
+
+    The generator is counter-based on the flat index, so any [T][1][N] shape of
+    the same size gives the same bytes; generating many rows lets every thread
+    take a share (threads split the rows).
+    """
+    rows = 1
+    while rows < 8192 and nbytes % (2 * rows) == 0:
+        rows *= 2
+    return gauss(nbytes // rows, 1, rows, sigma, seed, nthreads=nthreads).reshape(-1)
+
+
 def draw(seed: int, c: int) -> int:
     """Draw number c of the SplitMix64 stream seeded with `seed` (C implementation)."""
     return int(_load().synth_draw(seed, c))

@@ -78,23 +78,33 @@ def read_paper_numbers():
     return vals
 
 
-def freivalds_rows(V, w):
+def freivalds_rows(V, w, block_rows=1024):
     """(V w) per band for packed visibilities V int [F][N(N+1)/2][2] and complex weights w int64 [F][N][2],
     V extended to the full matrix by Hermitian symmetry. Exact: every partial sum is an integer below 2^53.
+    Works through the packed triangle a block of rows at a time (bounded memory at large N).
     Returns int64 [F][N][2]."""
     import numpy as np
     F, B, _ = V.shape
     N = int((np.sqrt(8 * B + 1) - 1) // 2)
-    iu, ju = np.triu_indices(N)
-    off = iu != ju
-    out = np.empty((F, N, 2), dtype=np.int64)
-    for b in range(F):
-        wc = w[b, :, 0] + 1j * w[b, :, 1]
-        Vc = V[b, :, 0].astype(np.float64) + 1j * V[b, :, 1].astype(np.float64)
-        t1 = Vc * wc[ju]                    # upper part: V_ij w_j into row i
-        t2 = np.conj(Vc[off]) * wc[iu[off]]  # lower part: conj(V_ij) w_i into row j
-        lr = np.bincount(iu, weights=t1.real, minlength=N) + np.bincount(ju[off], weights=t2.real, minlength=N)
-        li = np.bincount(iu, weights=t1.imag, minlength=N) + np.bincount(ju[off], weights=t2.imag, minlength=N)
-        out[b, :, 0] = np.rint(lr).astype(np.int64)
-        out[b, :, 1] = np.rint(li).astype(np.int64)
+    out = np.zeros((F, N, 2), dtype=np.int64)
+    for r0 in range(0, N, block_rows):
+        r1 = min(N, r0 + block_rows)
+        rows = np.arange(r0, r1)
+        lens = N - rows                                   # entries of row i: j = i .. N-1
+        p0 = r0 * N - r0 * (r0 - 1) // 2                  # packed index of (r0, r0)
+        iu = np.repeat(rows, lens)
+        ju = np.arange(lens.sum()) - np.repeat(np.cumsum(lens) - lens, lens) + iu
+        off = iu != ju
+        for b in range(F):
+            wc = w[b, :, 0] + 1j * w[b, :, 1]
+            seg = V[b, p0:p0 + lens.sum()]
+            Vc = seg[:, 0].astype(np.float64) + 1j * seg[:, 1].astype(np.float64)
+            t1 = Vc * wc[ju]                    # upper part: V_ij w_j into row i
+            t2 = np.conj(Vc[off]) * wc[iu[off]]  # lower part: conj(V_ij) w_i into row j
+            lr = np.bincount(iu - r0, weights=t1.real, minlength=r1 - r0)
+            li = np.bincount(iu - r0, weights=t1.imag, minlength=r1 - r0)
+            out[b, r0:r1, 0] += np.rint(lr).astype(np.int64)
+            out[b, r0:r1, 1] += np.rint(li).astype(np.int64)
+            out[b, :, 0] += np.rint(np.bincount(ju[off], weights=t2.real, minlength=N)).astype(np.int64)
+            out[b, :, 1] += np.rint(np.bincount(ju[off], weights=t2.imag, minlength=N)).astype(np.int64)
     return out

@@ -101,3 +101,31 @@ def test_large_n_tone_only_closed_form(xe):
     expect = int((qr * qr + qi * qi).sum())
     assert (V[:, :, 0] == expect).all()
     assert not V[:, :, 1].any()
+
+
+def test_max_n_sampled_autos_freivalds_and_closed_form(xe):
+    """N = CORR_MAX_N = 16384 (32,896 tiles per band, a 1.07 GB packed triangle): sampled entries at tile
+    edges and at random, every autocorrelation, and the Freivalds identity for every row against the oracle;
+    then one identical sequence on every element, whose visibilities are all (sum |q_t|^2, 0)."""
+    from conftest import freivalds_rows
+    N, F, T = xe.CORR_MAX_N, 1, 256
+    x = synth.gauss(N, F, T, 2.5, 1601)
+    V = run(xe, x)
+    rng = np.random.default_rng(16)
+    e = np.unique(np.concatenate([np.arange(0, N, 64), np.arange(63, N, 64)]))[::7]
+    ei, ej = np.meshgrid(e, e, indexing="ij")
+    keep = ei.ravel() <= ej.ravel()
+    ri, rj = rng.integers(0, N, 3000), rng.integers(0, N, 3000)
+    ii = np.concatenate([ei.ravel()[keep], np.minimum(ri, rj), np.arange(N)])
+    jj = np.concatenate([ej.ravel()[keep], np.maximum(ri, rj), np.arange(N)])
+    ff = np.zeros_like(ii)
+    assert np.array_equal(V[ff, xe.packed_index(N, ii, jj)].astype(np.int64),
+                          oracle.entries(x, np.stack([ff, ii, jj], 1)))
+    w = rng.integers(-3, 4, size=(F, N, 2)).astype(np.int64)
+    assert np.array_equal(freivalds_rows(V, w), oracle.freivalds_rhs(x, w))
+    # closed form: one sequence q_t on every element
+    q = synth.gauss(1, 1, T, 3.0, 1602)[:, 0, 0]
+    xs = np.repeat(q[:, None, None], N, axis=2).astype(np.uint8)
+    qr, qi = (q >> 4).astype(np.int64) - 8, (q & 15).astype(np.int64) - 8
+    Vs = run(xe, np.ascontiguousarray(xs))
+    assert (Vs[0, :, 0] == int((qr * qr + qi * qi).sum())).all() and not Vs[0, :, 1].any()

@@ -214,3 +214,38 @@ def test_batch_call(xe):
     for c, r in zip(cs, refs):
         assert_exact(c.readout().cpu().numpy(), r)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("host", [False, True], ids=["device", "host"])
+def test_overlapped_readouts(xe, host):
+    """Readouts overlapped with the next integration (two accumulator sets): five integrations of two
+    frames each, read out on a copy stream, each equal to the oracle; mixed with a plain readout; the
+    host-input path; destroy with a copy out still in flight."""
+    import torch
+    N, F, T = 96, 3, 333
+    frames = [synth.gauss(N, F, T, 2.5, 800 + k) for k in range(10)]
+    c = xe.Correlator(N, F, T)
+    cs = torch.cuda.Stream()
+    outs = []
+    for k in range(5):
+        for x in frames[2 * k:2 * k + 2]:
+            if k == 3:
+                c.accumulate_host(x)
+            else:
+                c.accumulate(to_dev(x))
+        if k == 2:  # a plain readout in between (with reset)
+            outs.append(c.readout(reset=True).cpu())
+            continue
+        o = torch.empty((F, xe.baselines(N), 2), dtype=torch.int32, device="cpu" if host else "cuda")
+        outs.append(c.readout_async(o.pin_memory() if host else o, cs))
+    cs.synchronize()
+    torch.cuda.synchronize()
+    for k, o in enumerate(outs):
+        ref = oracle.visibilities(frames[2 * k]) + oracle.visibilities(frames[2 * k + 1])
+        assert_exact(o.cpu().numpy(), ref)
+    # an empty integration reads as zeros; destroy waits for the copy out
+    z = torch.full((F, xe.baselines(N), 2), 5, dtype=torch.int32, device="cuda")
+    c.readout_async(z, cs)
+    c.close()
+    cs.synchronize()
+    assert not z.cpu().numpy().any()

@@ -68,13 +68,16 @@ def test_served_config4_shapes_bit_exact():
     xe.build()
     specs = [serve.StreamSpec(N, F) for N, F in SPECS]
     pool_bytes = 1 << 30
-    pool_np = synth.gauss(pool_bytes, 1, 1, 2.5, 1004).reshape(-1)
+    pool_np = synth.gauss_flat(pool_bytes, 2.5, 1004)
     pool = torch.from_numpy(pool_np).pin_memory()
     arrivals = make_arrivals(serve, 500.0, pool_bytes, 44)  # bursty: frames queue and share launches
     srv = serve.Server(specs, T_MAX, pool, budget_bytes=6 << 30, readout_every=FRAMES_PER_STREAM)
     srv.keep_readouts = True
+    srv.piece_bytes = 64 << 20  # most frames of these shapes then run in time pieces
+    assert max(len(srv.pieces(a)) for a in arrivals) == srv.max_pieces
     st = srv.run_served(arrivals)
-    assert st.frames == len(arrivals) and st.launches < len(arrivals)  # several frames shared launches
+    pieces = sum(len(srv.pieces(a)) for a in arrivals)
+    assert st.frames == len(arrivals) and st.launches < pieces  # several pieces shared launches
     served = [list(r) for r in srv.readouts]
     srv.close()
     rng = np.random.default_rng(45)

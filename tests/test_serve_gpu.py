@@ -17,7 +17,7 @@ def test_served_equals_alone_and_oracle():
     specs = [serve.StreamSpec(64, 4), serve.StreamSpec(128, 2), serve.StreamSpec(256, 1), serve.StreamSpec(64, 8)]
     t_max = 1024
     pool_bytes = 8 << 20
-    pool_np = synth.gauss(pool_bytes, 1, 1, 2.5, 4242).reshape(-1)
+    pool_np = synth.gauss_flat(pool_bytes, 2.5, 4242)
     pool = torch.from_numpy(pool_np).pin_memory()
     arrivals = serve.poisson_arrivals(2000.0, 96, len(specs), 256, t_max, pool_bytes, specs, 9)
     # served (bursty arrivals, so launches carry several frames), readout every 4 frames

@@ -61,3 +61,32 @@ def test_poisson_arrivals_recipe():
     assert all(a.offset + a.T * specs[a.stream].F * specs[a.stream].N <= 1 << 30 for a in arr)
     mean_gap = (arr[-1].t - arr[0].t) / 499
     assert 0.008 < mean_gap < 0.012
+
+
+def test_pieces_cover_each_frame_once():
+    """Time pieces of served frames: whole 256-sample blocks, in order, covering [0, T), at most max_pieces."""
+    from paper_1503_06203_gb300 import serve
+    srv = serve.Server.__new__(serve.Server)  # the piece rule needs only the specs and its knobs
+    srv.specs = [serve.StreamSpec(2048, 256), serve.StreamSpec(64, 1)]
+    srv.piece_bytes, srv.max_pieces = 512 << 20, 4
+    for sid, T in [(0, 8192), (0, 1024), (0, 256), (1, 100), (1, 8192), (0, 7936)]:
+        p = srv.pieces(serve.Arrival(0.0, sid, T, 0))
+        assert p[0][0] == 0 and p[-1][1] == T and 1 <= len(p) <= 4
+        assert all(a[1] == b[0] for a, b in zip(p, p[1:]))
+        assert all(u0 % 256 == 0 and u1 > u0 for u0, u1 in p)
+    assert len(srv.pieces(serve.Arrival(0.0, 0, 8192, 0))) == 4   # 4 GiB frame: capped at 4
+    assert len(srv.pieces(serve.Arrival(0.0, 1, 8192, 0))) == 1   # 0.5 MB frame: whole
+
+
+def test_piece_count_cost_model():
+    """Without a fixed piece size the count follows the copy rate: a slow link cuts a large frame into
+    pieces (its copy hides behind the correlation), a fast one keeps it nearly whole, small frames stay whole."""
+    from paper_1503_06203_gb300 import serve
+    srv = serve.Server.__new__(serve.Server)
+    srv.specs = [serve.StreamSpec(2048, 256), serve.StreamSpec(256, 16)]
+    srv.piece_bytes, srv.max_pieces, srv.piece_cost_ms, srv.hbm_gbs = 0, 4, 2.0, 6000.0
+    big, small = serve.Arrival(0.0, 0, 8192, 0), serve.Arrival(0.0, 1, 8192, 0)
+    srv.h2d_gbs = 20.0
+    assert srv.piece_count(big) == 4 and srv.piece_count(small) == 1
+    srv.h2d_gbs = 210.0
+    assert 1 <= srv.piece_count(big) <= 2 and srv.piece_count(small) == 1

@@ -46,3 +46,9 @@ def test_batched_recipe():
     assert all(f.N in synth.BATCH_N_CHOICES and 1 <= f.F <= 64 and 512 <= f.T <= 8192 and f.T % 256 == 0
                and 1.5 <= f.sigma <= 3.5 for f in fr)
     assert fr == synth.batched_frames()
+
+
+def test_gauss_flat_is_the_flat_generator():
+    """The multithreaded flat form gives the same bytes as one long row (the counter is the flat index)."""
+    for n in (1 << 16, 3 * 4096 + 256, 777):
+        assert np.array_equal(synth.gauss_flat(n, 2.5, 4242), synth.gauss(n, 1, 1, 2.5, 4242).reshape(-1))
