@@ -138,9 +138,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def effective_split(N: int, F: int, T: int, split: int, ctas: int) -> int:
+    """The time split a launch actually uses (0 = the library's automatic choice for this shape)."""
+    if split > 0:
+        return min(split, -(-T // 128))
+    import paper_1503_06203_gb300 as xe
+    items, _ = xe.plan_schedule(N, F, T, ctas)
+    nb = -(-N // 64)
+    return len(items) // (nb * (nb + 1) // 2 * F)
+
+
 def recorded_traffic(workload: str, product: int, split: int, mma_steps: int):
     """DRAM bytes per launch from the committed ncu summary of this workload, if taken on the current
-    kernel source with the same launch knobs (a time split changes the writers' traffic)."""
+    kernel source with the same launch knobs (a time split changes the writers' traffic; `split` is the
+    effective split, see effective_split)."""
     path = TRAFFIC_FILES.get(workload)
     if not path or not os.path.exists(path):
         return None
@@ -463,7 +474,9 @@ def single_frame_record(args, wl_key, frame, peaks, rank=0, world=1, bands=None,
     peak = (peaks["combo"] if hybrid else peaks["imma"]) / 1e12
     hw_ops = hardware_ops(N, Fb, T)
     hw_tops = hw_ops / (avg_kernel_ms * 1e-3) / 1e12
-    traffic = recorded_traffic(wl_key, product, split, mma_steps) if bands is None or Fb == F else None
+    ctas = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    traffic = (recorded_traffic(wl_key, product, effective_split(N, Fb, T, split, ctas), mma_steps)
+               if bands is None or Fb == F else None)
     hbm = (measured_peaks_file() or {}).get("hbm_gbs", 6699.8)
     rec = {
         "value": None, "ms_per_step": round(max_ms / args.steps, 4),
@@ -554,6 +567,7 @@ def run_xengine(args, wl_key):
                              "(16x the input)")
         line["large_n"] = ln
         line["batched"] = batched_record(args)
+        line["batched_small"] = batched_record(args, small=True)
         line["served"] = served_record(args)
         line["lags_gates"] = lags_gates_record(args)
     if rank == 0:
@@ -564,16 +578,17 @@ def run_xengine(args, wl_key):
 
 
 # ----------------------------------------------------------------------------- batched / served
-def batched_record(args) -> dict:
+def batched_record(args, small: bool = False) -> dict:
     """64 uneven frames: one launch per frame (back to back, no host waits) vs one batched
-    (graph-replayed) launch per step. Both modes run the same frames into the same handles."""
+    (graph-replayed) launch per step. Both modes run the same frames into the same handles.
+    small: the small-frame recipe (each frame microseconds of work) instead of the uneven-frame one."""
     import numpy as np
     import torch
 
     import oracle
     import paper_1503_06203_gb300 as xe
     import synth
-    frames = synth.batched_frames()
+    frames = synth.small_frames() if small else synth.batched_frames()
     cors = [xe.Correlator(f.N, f.F, f.T) for f in frames]
     xs_host = [f.make() for f in frames]
     xs = [torch.from_numpy(x).cuda() for x in xs_host]
@@ -623,11 +638,15 @@ def batched_record(args) -> dict:
         c.close()
     del xs
     torch.cuda.empty_cache()
+    workload = ("64 small frames (N 64..256, F 1..8, T 512..1024, sigma 1.5..3.5) per step" if small else
+                "64 uneven frames (N 64..2048, F 1..64, T 512..8192, sigma 1.5..3.5) per step")
+    in_bytes = sum(f.nbytes for f in frames)
     return {"metric": "Effective TOPS", "value": res["batched"]["effective_tops"], "unit": "TOPS",
             "steps": args.steps, "warmup": args.warmup,
-            "config": {"workload": "64 uneven frames (N 64..2048, F 1..64, T 512..8192, sigma 1.5..3.5) per step",
-                       "frames": len(frames), "effective_ops_per_step": ops,
-                       "l2": "inputs (6.1 GB per step) larger than L2, no flush"},
+            "config": {"workload": workload, "frames": len(frames), "effective_ops_per_step": ops,
+                       "input_bytes_per_step": in_bytes,
+                       "l2": ("inputs larger than L2, no flush" if in_bytes > 129e6 else
+                              "inputs smaller than L2 (resident across steps, as in a real stream of small frames)")},
             "batched": res["batched"], "plain": res["plain"],
             "speedup_batched_over_plain": round(res["plain"]["ms_per_step"] / res["batched"]["ms_per_step"], 3),
             "clocks": clocks}
@@ -658,7 +677,8 @@ def served_record(args) -> dict:
     sweeps = []
     sampler = ClockSampler(0).start()
     for rate in (float(r) for r in args.rates.split(",")):
-        count = args.served_frames or int(min(160, max(48, 6 * rate)))
+        # about 12 s of arrivals at low rates, 6 s at 40 frames/s, at most 240 frames
+        count = args.served_frames or int(min(240, max(120, 6 * rate)))
         arr = serve.poisson_arrivals(rate, count, len(specs), t_min, t_max, pool_bytes, specs,
                                      1004000 + int(round(10 * rate)))
         out = {"rate_hz": rate, "frames": count}

@@ -745,11 +745,17 @@ __global__ void __launch_bounds__(kThreads, 1) corr_tile_kernel(const __grid_con
       }
     }
     }
-    if (producer) {  // never leave with copies in flight (bounded)
+    if (producer) {
+      // Never leave with copies in flight: a bulk copy writes this CTA's shared
+      // memory, and the CTA lives until this thread returns, so waiting here
+      // for each armed barrier keeps every copy inside the CTA's lifetime. A
+      // copy in flight completes on its own; the wait is bounded all the same
+      // (also after a fault, when it may be the stuck barrier itself).
       const uint32_t first = issued > kStages ? issued - kStages : 0;
       for (uint32_t k = first; k < issued; ++k)
-        mbar_wait_bounded(&sm.full[k % kStages], (k / kStages) & 1, ok ? kSpinLimit : 1024u);
+        mbar_wait_bounded(&sm.full[k % kStages], (k / kStages) & 1, kSpinLimit);
     }
+    (void)ok;
     return;
   }
 

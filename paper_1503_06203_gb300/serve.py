@@ -174,7 +174,7 @@ class Server:
         self.rate_tops = 200.0  # effective TOPS assumed when estimating a frame's GPU time
         self.piece_bytes = 0     # 0: piece counts from the cost model (piece_count); else pieces of this many bytes
         self.max_pieces = 4
-        self.piece_cost_ms = 2.0
+        self.piece_cost_ms = 4.0
         self.h2d_gbs = 200.0     # host-to-device copy rate (measure_copy_rate sets it)
         self.hbm_gbs = 6000.0    # device memory rate for the accumulators' extra passes
         self.copy_stream = torch.cuda.Stream()
@@ -235,7 +235,8 @@ class Server:
 
         Pieces hide all but the first piece's copy behind the correlation; each
         extra piece costs one more read and write of the stream's accumulators
-        and a launch's fill and drain (piece_cost_ms, measured at about 2 ms).
+        and a launch's fill and drain (piece_cost_ms; traces on 2048 x 256
+        frames put the whole cost near 2.5 ms, and the default keeps a margin).
         The count maximises copy_ms (1 - 1/n) - (n - 1) cost, with copy_ms from
         the copy rate this server measured (h2d_gbs). piece_bytes, if set,
         instead cuts pieces of at least that many bytes (tests use it).

@@ -192,3 +192,23 @@ def batched_frames(count: int = 64, seed: int = 1003) -> list[Frame]:
         sigma = 1.5 + 2.0 * (d[3] >> 11) * 2.0 ** -53
         frames.append(Frame(N, F, T, "gauss", sigma, seed * 1000 + k))
     return frames
+
+
+SMALL_N_CHOICES = (64, 128, 256)
+
+
+def small_frames(count: int = 64, seed: int = 1005) -> list[Frame]:
+    """Small uneven frames: N from SMALL_N_CHOICES, F in 1..8, T in 512..1024 (multiple of 256), sigma in [1.5, 3.5].
+
+    Each frame alone is microseconds of work, too little to fill the GPU: the case batching is for.
+    Frame k's parameters come from draws 4k..4k+3 of stream `seed`; its samples from stream seed*1000+k.
+    """
+    frames = []
+    for k in range(count):
+        d = [draw(seed, 4 * k + i) for i in range(4)]
+        N = SMALL_N_CHOICES[d[0] % len(SMALL_N_CHOICES)]
+        F = 1 + d[1] % 8
+        T = 256 * (2 + d[2] % 3)
+        sigma = 1.5 + 2.0 * (d[3] >> 11) * 2.0 ** -53
+        frames.append(Frame(N, F, T, "gauss", sigma, seed * 1000 + k))
+    return frames

@@ -52,3 +52,11 @@ def test_gauss_flat_is_the_flat_generator():
     """The multithreaded flat form gives the same bytes as one long row (the counter is the flat index)."""
     for n in (1 << 16, 3 * 4096 + 256, 777):
         assert np.array_equal(synth.gauss_flat(n, 2.5, 4242), synth.gauss(n, 1, 1, 2.5, 4242).reshape(-1))
+
+
+def test_small_frames_recipe():
+    """Small uneven frames: seeded, within the recipe's ranges, and the same on every call."""
+    fr = synth.small_frames()
+    assert len(fr) == 64 and fr == synth.small_frames()
+    assert all(f.N in (64, 128, 256) and 1 <= f.F <= 8 and f.T in (512, 768, 1024) and 1.5 <= f.sigma <= 3.5
+               for f in fr)
