@@ -164,18 +164,17 @@ __device__ __forceinline__ uint4 lag_unit(const uint8_t* ring, int32_t t, const 
   uint32_t wv[4];
 #pragma unroll
   for (int w = 0; w < 4; ++w) {
-    uint32_t word = 0;
+    uint32_t v[4];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int k = 4 * w + b;
-      uint32_t v = ring[(tb + c[k]) & (kLagRingBytes - 1u)];
+      v[b] = ring[(tb + c[k]) & (kLagRingBytes - 1u)];
       if (!kInterior) {
         const int64_t src = static_cast<int64_t>(t) - lg[k];
-        if (src < 0 || src >= T) v = 0x88u;
+        if (src < 0 || src >= T) v[b] = 0x88u;
       }
-      word |= v << (8 * b);
     }
-    wv[w] = word;
+    wv[w] = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
   }
   // undo the rotation: output word j was read at step (j - rot) & 3
   uint4 o;
