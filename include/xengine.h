@@ -193,8 +193,8 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
 /*
  * corr_set_option -- per-handle launch knobs (the autotuner's controls; the
  * results do not depend on them):
- *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores for
- *     the first 96 of each 128-sample chunk and dp4a for the last 32, 2 = as 1
+ *   CORR_OPT_PRODUCT: 0 = tensor cores for every sample, 1 = tensor cores and
+ *     dp4a side by side (their shares: CORR_OPT_MMA_STEPS), 2 = as 1
  *     on the offset-encoded nibbles (unsigned operands, Sec. III.A's route):
  *     two extra kernels per call sum each element's nibbles over time and
  *     seed the output with the Eq. 3 offset terms (restated for the
@@ -208,11 +208,13 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
  *   CORR_OPT_MMA_STEPS: for product paths 1 and 2, how many of every 8
  *     k-steps of 32 samples (two 128-sample chunks) run on the tensor cores,
  *     the rest on dp4a: 8 = tensor cores only, 7 (chunks alternate 128/0 and
- *     96/32), 6 (the default, 96/32 in every chunk), 5 (alternate 64/64 and
- *     96/32), 4 (64/64). The two pipes run side by side on this GPU, so the
- *     share sets how the work is balanced between them. Single-frame calls
+ *     96/32), 6 (96/32 in every chunk), 5 (the default: alternate 64/64 and
+ *     96/32), 4 (64/64). Shares 5 and 4 apply to off-diagonal tiles; diagonal
+ *     tiles (bi == bj) keep 6. The two pipes run side by side on this GPU, so
+ *     the share sets how the work is balanced between them. Single-frame calls
  *     (corr_accumulate, corr_accumulate_host) on product path 1 take every
- *     share; batched and gated calls and product path 2 take 8 or 6 (other
+ *     share; batched calls and gated calls with periods of 128 samples or more
+ *     take 8, 6 or 5; other gated calls and product path 2 take 8 or 6 (other
  *     values run as 6).
  * A batched launch takes its product path and share from its first handle.
  * Returns CORR_OK, CORR_EINVAL or CORR_EBUSY.

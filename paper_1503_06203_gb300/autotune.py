@@ -8,10 +8,11 @@ of 8 k-steps of 32 samples, the rest on dp4a; each share is its own kernel
 instantiation, built in), and the time split (automatic, or a fixed number
 of ranges). For a frame shape (N, F, T)
 the tuner times every candidate with CUDA events on random frames and keeps
-the fastest in a JSON cache keyed by the GPU and the shape, so a shape is
-tuned once per GPU model. The library default (the first candidate) stays
-unless another candidate is at least MARGIN faster: candidates within timing
-noise of each other do not flip the choice from one tuning run to the next.
+the choice in a JSON cache keyed by the GPU and the shape, so a shape is
+tuned once per GPU model. The choice is the first candidate, in preference
+order (the library default first), within MARGIN of the fastest: candidates
+within timing noise of each other do not flip it from one tuning run to the
+next.
 """
 from __future__ import annotations
 
@@ -21,9 +22,9 @@ import os
 from . import CORR_OPT_MMA_STEPS, CORR_OPT_PRODUCT, CORR_OPT_SPLIT, Correlator
 
 CACHE_ENV = "XE_TUNE_CACHE"
-# (product path, tensor-core k-steps of 8): tensor cores + dp4a at every share (the library default, 6,
-# first), tensor cores alone, offset-encoded operands (Eq. 3)
-PATHS = ((1, 6), (1, 7), (1, 5), (1, 4), (0, 8), (2, 6))
+# (product path, tensor-core k-steps of 8), in order of preference: tensor cores + dp4a at every share (the
+# library default, 5, first), tensor cores alone, offset-encoded operands (Eq. 3)
+PATHS = ((1, 5), (1, 6), (1, 7), (1, 4), (0, 8), (2, 6))
 SPLITS = (0, 1, 2, 4)  # automatic, fixed
 MARGIN = 0.01          # relative speed-up a candidate needs over the default
 
@@ -38,8 +39,11 @@ def gpu_key() -> str:
     return f"{p.name}|sm_{p.major}{p.minor}|{p.multi_processor_count}sm"
 
 
+TUNER_VERSION = 2  # the candidate set and the kernels it chose among: entries of another version are not reused
+
+
 def shape_key(N: int, F: int, T: int) -> str:
-    return f"N{N}_F{F}_T{T}"
+    return f"N{N}_F{F}_T{T}_v{TUNER_VERSION}"
 
 
 def candidates(T: int):
@@ -95,9 +99,11 @@ def time_config(c: Correlator, x, product: int, mma_steps: int, split: int, reps
 
 
 def pick(trials: list[dict]) -> dict:
-    """The fastest trial, unless it beats the first (the library default) by less than MARGIN."""
-    fastest = min(trials, key=lambda d: d["ms"])
-    return fastest if fastest["ms"] < trials[0]["ms"] * (1.0 - MARGIN) else trials[0]
+    """The first trial, in preference order (the library default first, each path's automatic time
+    split before its fixed ones), within MARGIN of the fastest: candidates within timing noise of each
+    other do not flip the choice from one tuning run to the next."""
+    best = min(d["ms"] for d in trials)
+    return next(d for d in trials if d["ms"] <= best * (1.0 + MARGIN))
 
 
 def tune(N: int, F: int, T: int, reps: int = 5, path: str | None = None, force: bool = False) -> dict:

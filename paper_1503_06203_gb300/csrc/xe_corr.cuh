@@ -502,7 +502,8 @@ constexpr uint32_t kDiagR = 0xfa9050u, kDiagC = 0xfaedd8u, kDiagSel = 0xff990000
 // Split of a chunk's 128 samples between the tensor cores (k-steps of 32)
 // and dp4a (the rest), chosen per launch: the same split for every chunk, or
 // two splits alternating between consecutive chunks of a CTA, which gives the
-// finer average shares in between. Every split gives the same exact sums.
+// finer average shares in between. Shares 5 and 4 apply to off-diagonal
+// tiles; diagonal tiles keep 6. Every split gives the same exact sums.
 // Tensor-core k-steps per pair of chunks:
 enum : int {
   kSplitMma = 0,   // 8 of 8: tensor cores only
@@ -552,7 +553,10 @@ __device__ __forceinline__ void product_chunk(CorrSmem& sm, int buf, int warp, i
   const uint32_t b_side = smem_u32(sm.plane[buf][1][0]);
   const uint32_t b01 = diag ? a_base : b_side, b2 = b_side + kPsd * kPlaneBytes;
   const int ksteps = nvalid >= kTC ? kTC / 32 : (nvalid + 31) / 32;
-  const int split = kSplitT < 0 ? (hybrid == kSplitMma ? kSplitMma : kSplit6) : kSplitT;
+  // shares below 6 apply to off-diagonal tiles: a diagonal tile, with a quarter of its product warps
+  // idle and a quarter on single sub-tiles, runs best at 6 (measured)
+  const int split0 = kSplitT < 0 ? (hybrid == kSplitMma ? kSplitMma : kSplit6) : kSplitT;
+  const int split = diag && (split0 == kSplit5 || split0 == kSplit4) ? kSplit6 : split0;
   if (split != kSplitMma && ksteps == kTC / 32) {  // (a ragged last chunk takes the tensor-core path)
     const int mk = mma_ksteps(split, static_cast<int>(it & 1));
     if (sel == kSelAll)

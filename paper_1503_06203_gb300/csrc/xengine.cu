@@ -68,8 +68,10 @@ int device_setup(int dev) {
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit4>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGated, false>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGateArith, false>),
+                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGateArith, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, true>)})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
@@ -156,7 +158,7 @@ struct corr_handle {
   int64_t launches = 0;    // kernels launched by this handle
   int product = -1;        // CORR_OPT_PRODUCT (-1: library default)
   int split_opt = 0;       // CORR_OPT_SPLIT (0: automatic)
-  int mma_steps = 6;       // CORR_OPT_MMA_STEPS: tensor-core k-steps per 8 (the rest on dp4a)
+  int mma_steps = 5;       // CORR_OPT_MMA_STEPS: tensor-core k-steps per 8 (the rest on dp4a)
   int sticky = CORR_OK;
   int32_t* d_err = nullptr;
   cudaEvent_t last = nullptr;
@@ -582,7 +584,8 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
   return CORR_OK;
 }
 
-// kind: 1 = gate segments (corr_tile_kernel<kGated>), 2 = gate arithmetic (<kGateArith>).
+// kind: 1 = gate segments (corr_tile_kernel<kGated>), 2 = gate arithmetic (<kGateArith>; share 5 in
+// its own instantiation).
 int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid, int kind) {
   if (b.exec) {
     cudaGraphExecDestroy(b.exec);
@@ -614,8 +617,9 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = kind == 2 ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false>)
-                      : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>);
+  kp.func = kind == 1   ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>)
+            : hybrid == xe::kSplit5 ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false, xe::kSplit5>)
+                                    : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -717,8 +721,10 @@ int ring_set_items(RingSet& r, int64_t nitems, cudaStream_t st) {
   return CORR_OK;
 }
 
+// Batched launches run share 5 in its own instantiation, or kSplitMma / kSplit6 chosen at run time
+// (other shares run as 6).
 void* corr_kernel_fn(int hybrid) {
-  (void)hybrid;  // batched launches run kSplitMma or kSplit6, chosen at run time
+  if (hybrid == xe::kSplit5) return reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false, xe::kSplit5>);
   return reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false>);
 }
 
@@ -889,7 +895,7 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
   a.B = 0;
   a.vis = nullptr;
   a.fresh = 0;
-  a.hybrid = hybrid == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
+  a.hybrid = hybrid == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;  // (the runtime-split instantiation's choice)
   a.err = hs[0]->d_err;
   if ((rc = ring_set_launch(r, hybrid, st))) return rc;
   ring.next = (ring.next + 1) % kBatchSets;
@@ -966,7 +972,8 @@ int gated_arith_launch(corr_handle_t* const* gates, int G, const CUtensorMap& ma
     d.G = G;
     d.gate = g;
   }
-  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps) == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
+  int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps);
+  if (hybrid != xe::kSplitMma && hybrid != xe::kSplit5) hybrid = xe::kSplit6;
   if (!b.exec || b.key_frames != G || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_gated != 2 || b.key_err != h0->d_err)
     if ((rc = build_graph(b, G, nitems, grid, h0->d_err, hybrid, 2))) return rc;
@@ -1128,7 +1135,7 @@ int gated_impl(corr_handle_t* const* gates, int G, const uint8_t* in, int32_t T,
     d.t0 = empty ? 1 : segs[s].t0;  // t0 > T: nothing is valid
     d.atomic = 0;
   }
-  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps);
+  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps) == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
   if (!b.exec || b.key_frames != nseg || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_gated != 1 || b.key_err != h0->d_err)
     if ((rc = build_graph(b, nseg, nitems, grid, h0->d_err, hybrid, 1))) return rc;

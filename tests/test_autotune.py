@@ -10,9 +10,9 @@ def test_cache_roundtrip_and_candidates(tmp_path):
     p = str(tmp_path / "tune.json")
     assert autotune.load_cache(p) == {}
     autotune.save_cache({"gpu": {autotune.shape_key(256, 4, 100): {"product": 0, "split": 2}}}, p)
-    assert autotune.load_cache(p)["gpu"]["N256_F4_T100"]["split"] == 2
+    assert autotune.load_cache(p)["gpu"][f"N256_F4_T100_v{autotune.TUNER_VERSION}"]["split"] == 2
     cands = autotune.candidates(4096)
-    assert cands[0] == (1, 6, 0)  # the library default is tried first
+    assert cands[0] == (1, 5, 0)  # the library default is tried first
     assert (1, 6, 4) in cands and (0, 8, 0) in cands and {m for _, m, _ in cands} == {4, 5, 6, 7, 8}
     assert all(s <= 1 for _, _, s in autotune.candidates(128))  # one chunk: no splits beyond 1
 
@@ -24,6 +24,8 @@ def test_pick_keeps_default_within_margin():
     assert autotune.pick(trials) is trials[0]  # 0.4% faster: within the margin
     trials[1]["ms"] = 5.0
     assert autotune.pick(trials) is trials[1]  # 5.7% faster: taken
+    trials.append({"product": 0, "split": 1, "ms": 4.99})
+    assert autotune.pick(trials) is trials[1]  # the earlier of two within the margin of the fastest
 
 
 @pytest.mark.gpu

@@ -93,13 +93,14 @@ def test_band_handles_batched_and_gated(xe):
     V = np.concatenate([c.readout().cpu().numpy() for c in parts], axis=0)
     assert np.array_equal(V.astype(np.int64), oracle.visibilities(x_np))
     assert np.array_equal(other.readout().cpu().numpy().astype(np.int64), oracle.visibilities(other_np))
-    # gated: gate handles over bands [1, 3)
-    G, period, phase = 3, 96, 10
-    gates = [xe.Correlator(N, F, T, bands=(1, 3)) for _ in range(G)]
-    xe.accumulate_gated(gates, x, period, phase)
-    ref = oracle.gated(np.ascontiguousarray(x_np[:, 1:3, :]), G, period, phase)
-    for g in range(G):
-        assert np.array_equal(gates[g].readout().cpu().numpy().astype(np.int64), ref[g]), g
+    # gated: gate handles over bands [1, 3), a period below one chunk (gate segments) and one above
+    # (gate arithmetic)
+    for G, period, phase in [(3, 96, 10), (4, 256, 200)]:
+        gates = [xe.Correlator(N, F, T, bands=(1, 3)) for _ in range(G)]
+        xe.accumulate_gated(gates, x, period, phase)
+        ref = oracle.gated(np.ascontiguousarray(x_np[:, 1:3, :]), G, period, phase)
+        for g in range(G):
+            assert np.array_equal(gates[g].readout().cpu().numpy().astype(np.int64), ref[g]), (period, g)
     torch.cuda.synchronize()
 
 

@@ -73,3 +73,34 @@ def test_device_wait_runs_out_and_the_context_survives(xe):
         V = c.readout().cpu().numpy().astype(np.int64)
         assert c.status() == 0
     assert np.array_equal(V, oracle.visibilities(x))
+
+
+def test_split_change_on_a_busy_handle_is_refused(xe):
+    """Changing the time split rebuilds the schedule, so the handle must be idle: while a long correlation
+    is still running the call returns CORR_EBUSY and changes nothing; once it is done the change is taken,
+    and the results stay exact."""
+    import torch
+
+    import oracle
+    import synth
+    from paper_1503_06203_gb300._lib import CORR_EBUSY
+    N, F, T = 2048, 16, 16384  # about 0.3 s of work
+    x = torch.zeros((T, F, N), dtype=torch.uint8, device="cuda")
+    c = xe.Correlator(N, F, T)
+    torch.cuda.synchronize()
+    c.accumulate(x)
+    with pytest.raises(xe.XEngineError) as ei:
+        c.set_option(xe.CORR_OPT_SPLIT, 2)
+    assert ei.value.code == CORR_EBUSY and c.get_option(xe.CORR_OPT_SPLIT) == 0
+    c.synchronize()
+    c.set_option(xe.CORR_OPT_SPLIT, 2)
+    assert c.get_option(xe.CORR_OPT_SPLIT) == 2
+    small = synth.gauss(200, 2, 300, 2.5, 9)
+    with xe.Correlator(200, 2, 300) as d:
+        d.accumulate(torch.from_numpy(small).cuda())
+        d.synchronize()
+        d.set_option(xe.CORR_OPT_SPLIT, 2)
+        d.reset()
+        d.accumulate(torch.from_numpy(small).cuda())
+        assert np.array_equal(d.readout().cpu().numpy().astype(np.int64), oracle.visibilities(small))
+    c.close()
