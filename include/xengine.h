@@ -213,8 +213,7 @@ int corr_shift_lags(const uint8_t* in_dev, uint8_t* out_dev, int32_t N, int32_t 
  *     tiles (bi == bj) keep 6. The two pipes run side by side on this GPU, so
  *     the share sets how the work is balanced between them. Single-frame calls
  *     (corr_accumulate, corr_accumulate_host) on product path 1 take every
- *     share; batched calls and gated calls with periods of 128 samples or more
- *     take 8, 6 or 5; other gated calls and product path 2 take 8 or 6 (other
+ *     share; batched and gated calls and product path 2 take 8 or 6 (other
  *     values run as 6).
  * A batched launch takes its product path and share from its first handle.
  * Returns CORR_OK, CORR_EINVAL or CORR_EBUSY.

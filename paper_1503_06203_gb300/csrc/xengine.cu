@@ -68,10 +68,8 @@ int device_setup(int dev) {
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, false, xe::kSplit4>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false>),
-                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kBatch, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGated, false>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGateArith, false>),
-                        reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kGateArith, false, xe::kSplit5>),
                         reinterpret_cast<const void*>(xe::corr_tile_kernel<xe::kSingle, true>)})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
@@ -584,8 +582,7 @@ int grow_set(BatchSet& b, size_t frames, size_t items) {
   return CORR_OK;
 }
 
-// kind: 1 = gate segments (corr_tile_kernel<kGated>), 2 = gate arithmetic (<kGateArith>; share 5 in
-// its own instantiation).
+// kind: 1 = gate segments (corr_tile_kernel<kGated>), 2 = gate arithmetic (<kGateArith>).
 int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int32_t* err, int hybrid, int kind) {
   if (b.exec) {
     cudaGraphExecDestroy(b.exec);
@@ -617,9 +614,8 @@ int build_graph(BatchSet& b, int64_t nframes, int64_t nitems, int64_t grid, int3
   void* params[2] = {&unused, &a};
   cudaKernelNodeParams kp;
   memset(&kp, 0, sizeof kp);
-  kp.func = kind == 1   ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>)
-            : hybrid == xe::kSplit5 ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false, xe::kSplit5>)
-                                    : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false>);
+  kp.func = kind == 1 ? reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGated, false>)
+                      : reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kGateArith, false>);
   kp.gridDim = dim3(static_cast<unsigned>(grid));
   kp.blockDim = dim3(xe::kThreads);
   kp.sharedMemBytes = static_cast<unsigned>(kSmemBytes);
@@ -721,10 +717,10 @@ int ring_set_items(RingSet& r, int64_t nitems, cudaStream_t st) {
   return CORR_OK;
 }
 
-// Batched launches run share 5 in its own instantiation, or kSplitMma / kSplit6 chosen at run time
-// (other shares run as 6).
+// Batched launches run kSplitMma or kSplit6, chosen at run time (other shares run as 6: a share-5
+// instantiation of the batch kernel spilled and measured slower than share 6).
 void* corr_kernel_fn(int hybrid) {
-  if (hybrid == xe::kSplit5) return reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false, xe::kSplit5>);
+  (void)hybrid;
   return reinterpret_cast<void*>(xe::corr_tile_kernel<xe::kBatch, false>);
 }
 
@@ -972,8 +968,7 @@ int gated_arith_launch(corr_handle_t* const* gates, int G, const CUtensorMap& ma
     d.G = G;
     d.gate = g;
   }
-  int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps);
-  if (hybrid != xe::kSplitMma && hybrid != xe::kSplit5) hybrid = xe::kSplit6;
+  const int hybrid = chunk_hybrid_flag(h0->product, h0->mma_steps) == xe::kSplitMma ? xe::kSplitMma : xe::kSplit6;
   if (!b.exec || b.key_frames != G || b.key_items != nitems || b.key_grid != grid || b.key_hybrid != hybrid ||
       b.key_gated != 2 || b.key_err != h0->d_err)
     if ((rc = build_graph(b, G, nitems, grid, h0->d_err, hybrid, 2))) return rc;
