@@ -170,6 +170,7 @@ struct corr_handle {
   // host-input path: two device chunk buffers, two streams
   uint8_t* hchunk[2] = {nullptr, nullptr};
   int32_t hchunk_T = 0, tail_T = 0;
+  uint32_t hseq = 0;  // chunks copied so far: chunk buffers alternate across calls
   cudaStream_t s_copy = nullptr, s_comp = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
   // offset-encoded route: per-element nibble sums [F][N][2] of the current launch
@@ -1202,10 +1203,14 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
   const size_t row = static_cast<size_t>(h->F_in) * h->N;  // bytes per time sample (host layout)
   const size_t band0 = static_cast<size_t>(h->f0) * h->N;  // the handle's first band within a time sample
   if (!h->s_copy) {
-    // chunk of about T/2 samples (a stage multiple), at most 1 GiB per buffer:
-    // with copies overlapping the previous frame, the correlation is the
-    // longer chain, and larger chunks run it more efficiently
-    int64_t cT = ceil_div(ceil_div(h->T, 2), xe::kTC) * xe::kTC;
+    // Time chunks of at most 1 GiB per buffer (a stage multiple). Each chunk
+    // after the first adds onto the output once more, so the frame is split
+    // in two (the copy of one half overlapping the correlation of the other)
+    // only where its input outweighs its output; otherwise it is one chunk,
+    // and the next call's copy (into the other buffer) overlaps this call's
+    // correlation.
+    const int64_t in_bytes = int64_t(h->T) * h->F * Np, out_bytes = int64_t(h->F) * h->B * 2 * 4;
+    int64_t cT = in_bytes > out_bytes ? ceil_div(ceil_div(h->T, 2), xe::kTC) * xe::kTC : h->T;
     const int64_t cap = std::max<int64_t>(xe::kTC, ((int64_t(1) << 30) / (int64_t(h->F) * Np)) / xe::kTC * xe::kTC);
     cT = std::max<int64_t>(xe::kTC, std::min<int64_t>(cT, cap));
     cT = std::min<int64_t>(cT, ceil_div(h->T, xe::kTC) * xe::kTC);
@@ -1235,11 +1240,11 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
   XE_CHECK(h, cudaStreamWaitEvent(h->s_comp, h->ev_in, 0));
   const int32_t nchunks = static_cast<int32_t>(ceil_div(h->T, h->hchunk_T));
   for (int32_t c = 0; c < nchunks; ++c) {
-    const int b = c & 1;
+    const int b = static_cast<int>((h->hseq + static_cast<uint32_t>(c)) & 1);
     const int32_t t0 = c * h->hchunk_T;
     const int32_t cT = std::min(h->hchunk_T, h->T - t0);
-    // buffer b's last reader: chunk c - 2 of this call, or the last chunk on b
-    // of an earlier call (an event never recorded is passed at once)
+    // buffer b's last reader: the chunk two before this one, in this call or
+    // an earlier one (an event never recorded is passed at once)
     XE_CHECK(h, cudaStreamWaitEvent(h->s_copy, h->ev_used[b], 0));
     // into the chunk buffer [cT][F][Np]: the handle's bands of each time sample
     const uint8_t* src = packed_host + static_cast<size_t>(t0) * row + band0;
@@ -1267,6 +1272,7 @@ int corr_accumulate_host(corr_handle_t* h, const uint8_t* packed_host, void* str
       return rc;
     XE_CHECK(h, cudaEventRecord(h->ev_used[b], h->s_comp));
   }
+  h->hseq += static_cast<uint32_t>(nchunks);
   // the caller's stream continues after the last chunk
   XE_CHECK(h, cudaEventRecord(h->last, h->s_comp));
   XE_CHECK(h, cudaStreamWaitEvent(st, h->last, 0));

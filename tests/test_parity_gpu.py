@@ -155,11 +155,14 @@ def test_host_input_path(xe, N, F, T):
     assert_exact(out, 2 * oracle.visibilities(x))
 
 
-def test_host_frames_back_to_back(xe):
+# (192, 8, 4096): input larger than output, two time chunks per frame; the others: output
+# larger, one chunk per frame, so consecutive calls alternate the two chunk buffers
+# ((512, 2, 300) with a ragged chunk, (100, 3, 200) with N % 16 != 0, rows padded in the copy)
+@pytest.mark.parametrize("N,F,T", [(192, 8, 4096), (512, 2, 300), (100, 3, 200)])
+def test_host_frames_back_to_back(xe, N, F, T):
     """Frame k+1's copies may overlap frame k's correlation and readout: each readout still
     holds exactly its own frame."""
     import torch
-    N, F, T = 192, 8, 4096
     frames = [synth.gauss(N, F, T, 2.0 + 0.5 * k, 80 + k) for k in range(4)]
     pinned = [torch.from_numpy(x).pin_memory() for x in frames]
     outs = [torch.empty((F, xe.baselines(N), 2), dtype=torch.int32).pin_memory() for _ in frames]
