@@ -245,6 +245,16 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // accumulator layout, so its dp4a work is those entries' dot products. The
 // dp4a work comes in blocks of 8 samples of one plane; the MMAs are spread
 // evenly over the blocks.
+// The dp4a block order: block k of a chunk with kMmaK tensor-core k-steps
+// works on plane (e & 3), samples group (e >> 2), e = 5 bits of the table.
+// The order keeps each block off the accumulators of the MMAs issued in it
+// (and mostly in the block before), whose results are still in flight, and
+// changes plane between consecutive blocks where it can.
+__device__ __forceinline__ constexpr uint32_t dp4a_block(int mk, int k) {
+  return static_cast<uint32_t>(((k < 12 ? (mk == 3 ? 0x6b1c94114501841ull : 0x6b12e4288628820ull)
+                                        : 0xe7bb8d6695b4251ull) >> (5 * (k % 12))) & 31u);
+}
+
 template <int sel, int kMmaK, bool kEnc>
 __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base, uint32_t b2_base, int pr, int pc,
                                              int lane, int32_t (&acc)[3][2][4]) {
@@ -272,7 +282,8 @@ __device__ __forceinline__ void chunk_hybrid(uint32_t a_base, uint32_t b01_base,
       if (sub_on(sel, mni)) mma_8bit<kEnc>(acc[mpl][mni], fa[0], fa[1], fa[2], fa[3], fb[mni][0], fb[mni][1]);
     }
     // ---- integer ALU: samples 32*kMmaK + 8*grp .. +7 of plane dpl ----
-    const int grp = k / 3, dpl = k % 3;
+    const uint32_t ord = dp4a_block(kMmaK, k);
+    const int grp = static_cast<int>(ord >> 2), dpl = static_cast<int>(ord & 3);
     const int s0 = 32 * kMmaK + 8 * grp, chunk = s0 >> 4, inner = s0 & 15;
     const uint32_t pa = a_base + dpl * kPlaneBytes;
     const uint32_t pb = dpl < 2 ? b01_base + dpl * kPlaneBytes : b2_base;
