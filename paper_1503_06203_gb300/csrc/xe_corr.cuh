@@ -249,7 +249,8 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // works on plane (e & 3), samples group (e >> 2), e = 5 bits of the table.
 // The order keeps each block off the accumulators of the MMAs issued in it
 // (and mostly in the block before), whose results are still in flight, and
-// changes plane between consecutive blocks where it can.
+// changes plane between consecutive blocks where it can (dp4a_order.py
+// beside this file states the criterion and regenerates the table).
 __device__ __forceinline__ constexpr uint32_t dp4a_block(int mk, int k) {
   return static_cast<uint32_t>(((k < 12 ? (mk == 3 ? 0x6b1c94114501841ull : 0x6b12e4288628820ull)
                                         : 0xe7bb8d6695b4251ull) >> (5 * (k % 12))) & 31u);

@@ -118,3 +118,26 @@ def test_schedule_covers_every_unit_once(xe, N, F, T, ctas):
     load = np.bincount(np.arange(len(items)) % grid, weights=cost, minlength=grid)
     if len(items) >= 4 * grid:
         assert load.max() <= 1.06 * load.mean()
+
+
+def test_dp4a_block_order_table_is_a_permutation():
+    """The dp4a block order in xe_corr.cuh visits every (plane, 8-sample group) of a chunk's dp4a
+    share exactly once, for both k-step counts, and keeps blocks off the MMAs issued in them."""
+    import importlib.util
+    import re
+    csrc = os.path.join(ROOT, "paper_1503_06203_gb300", "csrc")
+    src = open(os.path.join(csrc, "xe_corr.cuh")).read()
+    m = re.search(r"mk == 3 \? (0x[0-9a-f]+)ull : (0x[0-9a-f]+)ull\)\s*:\s*(0x[0-9a-f]+)ull", src)
+    assert m, "dp4a_block table not found"
+    w3, w2lo, w2hi = (int(g, 16) for g in m.groups())
+    spec = importlib.util.spec_from_file_location("dp4a_order", os.path.join(csrc, "dp4a_order.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    for mk, words in ((3, (w3, 0)), (2, (w2lo, w2hi))):
+        planes = gen.mma_planes(mk)
+        nb = len(planes)
+        ent = [(words[k // 12] >> (5 * (k % 12))) & 31 for k in range(nb)]
+        assert sorted((e & 3, e >> 2) for e in ent) == sorted((p, g) for p in range(3) for g in range(nb // 3))
+        order = [e & 3 for e in ent]
+        assert all(p not in {pl for pl, _ in planes[k]} for k, p in enumerate(order)), mk
+        assert gen.pack(order) == [words[0], words[1]]
