@@ -10,12 +10,13 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_MAX_SAMPLES, CORR_OK,
-                   CORR_OPT_MMA_STEPS, CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
+from ._lib import (CORR_BATCH_ALONE_WAVES, CORR_EINVAL, CORR_EOVERFLOW, CORR_ETIMEOUT, CORR_MAX_N, CORR_MAX_SAMPLES,
+                   CORR_OK, CORR_OPT_MMA_STEPS, CORR_OPT_PRODUCT, CORR_OPT_SPLIT, XEngineError, check, last_error, lib)
 
 __all__ = ["Correlator", "accumulate_batch", "plan_tiles", "effective_ops", "baselines", "packed_index",
            "plan_schedule", "correlate_noalloc", "selftest_wait_timeout", "shift_lags", "accumulate_gated",
            "band_range", "CORR_OPT_PRODUCT", "CORR_OPT_SPLIT", "CORR_OPT_MMA_STEPS", "XEngineError", "CORR_MAX_SAMPLES", "CORR_MAX_N",
+           "CORR_BATCH_ALONE_WAVES", "batch_runs_alone",
            "build", "last_error"]
 
 
@@ -260,10 +261,12 @@ def selftest_wait_timeout(polls: int = 4096, stream=None) -> int:
 
 
 def accumulate_batch(correlators, inputs, stream=None):
-    """One launch for several frames: inputs[k] (device uint8 [T_k][F][N]) is added to correlators[k].
+    """Several frames in one call: inputs[k] (device uint8 [T_k][F][N]) is added to correlators[k].
 
-    T_k may differ from the correlator's T (frames of varying length); the
-    correlators must be distinct.
+    The frames share one batched launch, except that a frame of its correlator's
+    full T which fills the GPU on its own (batch_runs_alone) is launched alone
+    first, through the single-frame kernel. T_k may differ from the correlator's
+    T (frames of varying length); the correlators must be distinct.
     """
     n = len(correlators)
     assert len(inputs) == n
@@ -274,3 +277,10 @@ def accumulate_batch(correlators, inputs, stream=None):
     xs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in inputs])
     Ts = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in inputs])
     check(lib().corr_accumulate_batch_ex(hs, xs, Ts, n, _stream_ptr(stream)))
+
+
+def batch_runs_alone(N: int, F: int, sms: int) -> bool:
+    """Whether accumulate_batch launches a frame of its handle's full T alone (single-frame kernel):
+    its whole 64 x 64 tiles number at least CORR_BATCH_ALONE_WAVES per SM."""
+    nb = -(-N // 64)
+    return nb * (nb + 1) // 2 * F >= CORR_BATCH_ALONE_WAVES * sms

@@ -19,6 +19,7 @@ CORR_OPT_PRODUCT = 1
 CORR_OPT_SPLIT = 2
 CORR_OPT_MMA_STEPS = 3
 CORR_MAX_SAMPLES = 16777215
+CORR_BATCH_ALONE_WAVES = 4
 
 # (name, restype, argtypes) for every symbol include/xengine.h declares
 _vp, _i32, _i64, _int = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int

@@ -776,6 +776,29 @@ int ring_set_launch(RingSet& r, int hybrid, cudaStream_t st) {
   return CORR_OK;
 }
 
+static int batch_shared(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
+                        cudaStream_t st);
+
+// One frame through the single-frame kernel (the body of corr_accumulate, its
+// checks done by the caller).
+static int accumulate_alone(corr_handle_t* h, const uint8_t* packed_dev, cudaStream_t st) {
+  int rc = order_after_last(h, st);
+  if (rc) return rc;
+  const uint8_t* frame;
+  int32_t np;
+  int64_t row_bytes;
+  if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np, &row_bytes))) return rc;
+  if ((rc = launch_frame(h, frame, np, row_bytes, h->plan, st))) return rc;
+  h->samples += h->T;
+  return record_last(h, st);
+}
+
+// Whole tiles per CTA slot from which a frame runs alone: its tiles then fill
+// every SM four times over, so it gains nothing from sharing a launch, and the
+// single-frame kernel (no frame descriptors or chunk metadata, tensor-core
+// share 5 built) runs it faster than the batched one.
+constexpr int64_t kAloneWaves = CORR_BATCH_ALONE_WAVES;
+
 int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n, void* stream) {
   if (n < 0 || (n > 0 && (!hs || !inputs))) return fail(CORR_EINVAL, "bad batch arguments");
   if (n == 0) return CORR_OK;
@@ -796,6 +819,34 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
       if (hs[j] == hs[k]) return fail(CORR_EINVAL, "batch handles must be distinct (frames %d and %d)", j, k);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // frames that fill the GPU on their own (at their handle's T) run alone, in
+  // order, on the stream; the rest share one batched launch after them
+  const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
+  std::vector<corr_handle_t*> sh;
+  std::vector<const uint8_t*> si;
+  std::vector<int32_t> sT;
+  for (int k = 0; k < n; ++k) {
+    corr_handle* h = hs[k];
+    const int32_t Tk = Ts ? Ts[k] : h->T;
+    const int64_t nb = ceil_div(h->N, xe::kTile);
+    if (Tk == h->T && nb * (nb + 1) / 2 * h->F >= kAloneWaves * slots) {
+      int rc = accumulate_alone(h, inputs[k], st);
+      if (rc) return rc;
+    } else {
+      sh.push_back(h);
+      si.push_back(inputs[k]);
+      sT.push_back(Tk);
+    }
+  }
+  if (sh.empty()) return CORR_OK;
+  return batch_shared(sh.data(), si.data(), sT.data(), static_cast<int>(sh.size()), st);
+}
+
+// The batched launch: one work list over every frame's items, built on the
+// device, one correlator launch (checks done by batch_impl).
+static int batch_shared(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
+                        cudaStream_t st) {
+  const int dev = hs[0]->device;
   const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
   // Per frame: tiles, chunks, and a time split that keeps its items short
   // against a CTA's share of the whole batch (a frame with few tiles and a

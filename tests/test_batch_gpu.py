@@ -140,3 +140,26 @@ def test_batch_time_split_and_ring_reuse(xe):
             assert np.array_equal(cors[i].readout(reset=True).cpu().numpy().astype(np.int64),
                                   oracle.visibilities(x)), (k, i)
     torch.cuda.synchronize()
+
+
+def test_batch_frames_that_fill_the_gpu_run_alone(xe):
+    """Frames whose tiles fill every SM CORR_BATCH_ALONE_WAVES times run alone (single-frame kernel),
+    the rest share the batched launch: every result equals the oracle, twice in a row (adds onto
+    resident sums), with the routes mixed in one call. A large frame of fewer samples than its
+    handle's T stays in the shared launch."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    big_f = -(-xe.CORR_BATCH_ALONE_WAVES * sms // 36)  # N = 512: 36 tiles per band
+    shapes = [(512, big_f, 256), (64, 2, 300), (1024, -(-xe.CORR_BATCH_ALONE_WAVES * sms // 136), 128),
+              (200, 3, 1000), (512, big_f, 384)]
+    alone = [xe.batch_runs_alone(N, F, sms) for N, F, _ in shapes]
+    assert alone == [True, False, True, False, True]
+    cors = [xe.Correlator(N, F, T) for N, F, T in shapes]
+    xs = [synth.gauss(N, F, T, 2.5, 900 + k) for k, (N, F, T) in enumerate(shapes)]
+    xs[4] = np.ascontiguousarray(xs[4][:200])  # 200 of the handle's 384 samples: shared launch
+    xd = [torch.from_numpy(x).cuda() for x in xs]
+    for _ in range(2):
+        xe.accumulate_batch(cors, xd)
+    for k, (c, x) in enumerate(zip(cors, xs)):
+        assert np.array_equal(c.readout().cpu().numpy().astype(np.int64), 2 * oracle.visibilities(x)), k
+    torch.cuda.synchronize()
