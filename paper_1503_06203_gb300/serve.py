@@ -260,7 +260,7 @@ class Server:
         return [(bounds[k], bounds[k + 1]) for k in range(n)]
 
     def run_served(self, arrivals: list[Arrival], max_inflight: int = 3, small_ms: float = 2.0,
-                   trace_gpu: bool = False) -> RunStats:
+                   trace_gpu: bool = False, join_frac: float = 0.25) -> RunStats:
         recs = [FrameRecord(a.t) for a in arrivals]
         pending = collections.deque(range(len(arrivals)))  # not yet arrived
         waiting = collections.deque()   # arrived, waiting for budget
@@ -318,7 +318,7 @@ class Server:
             # arrival order. All pieces of a launch finish together, so the launch stays close to FIFO:
             # a piece whose work is more than the launch's so far (and more than small_ms) starts the next
             # launch instead (older work never waits for a larger, younger piece), and younger pieces join
-            # the oldest one only up to a quarter of its work, or small_ms (a younger frame never holds up
+            # the oldest one only up to join_frac of its work, or small_ms (a younger frame never holds up
             # an older one by much)
             if ready and len(inflight) < max_inflight:
                 chosen, seen, rest, work, cut = [], set(), [], 0.0, False
@@ -329,7 +329,7 @@ class Server:
                     w = self.frame_ms(a) * (u1 - u0) / a.T
                     eligible = a.stream not in seen and order[a.stream][0] == k and launched[k] == p
                     if cut or not eligible or (chosen and (w > max(work, small_ms)
-                                                           or work - head + w > max(small_ms, 0.25 * head))):
+                                                           or work - head + w > max(small_ms, join_frac * head))):
                         cut = cut or eligible
                         rest.append((k, p))
                     else:
