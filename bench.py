@@ -48,7 +48,7 @@ WORKLOADS = {
     "pathfinder": ("PATHFINDER", "Pathfinder shape N=256 F=256 T=16384, Gaussian sigma=2.5 levels, one frame per launch"),
     "large_n": ("LARGE_N", "large N: N=8192 F=4 T=2048, sigma=2.5 plus a common tone, one frame per launch"),
 }
-EXTRA_WORKLOADS = ("batched", "served", "lags_gates")
+EXTRA_WORKLOADS = ("batched", "batched_small", "served", "lags_gates")
 KERNEL_NAME = "corr_tile_kernel"
 KERNEL_SOURCES = ["paper_1503_06203_gb300/csrc/xe_corr.cuh", "paper_1503_06203_gb300/csrc/xe_ptx.cuh"]
 TRAFFIC_FILES = {"pathfinder": os.path.join(ROOT, "profiles", "corr_tile_kernel_pathfinder.md"),
@@ -788,7 +788,7 @@ def _standalone(args, metric, unit, rec):
 def run_batched(args):
     import paper_1503_06203_gb300 as xe
     xe.build()
-    rec = batched_record(args)
+    rec = batched_record(args, small=args.workload == "batched_small")
     _standalone(args, rec.pop("metric"), rec.pop("unit"), rec)
 
 
@@ -812,7 +812,7 @@ def main():
     args = parse_args()
     if args.workload == "lags_gates":
         run_lags_gates(args)
-    elif args.workload == "batched":
+    elif args.workload in ("batched", "batched_small"):
         run_batched(args)
     elif args.workload == "served":
         run_served(args)

@@ -155,7 +155,13 @@ int corr_readout_host(corr_handle_t* h, int32_t* vis_host, int reset, void* stre
 int corr_readout_async(corr_handle_t* h, int32_t* vis_dev, void* copy_stream);
 int corr_readout_host_async(corr_handle_t* h, int32_t* vis_host, void* copy_stream);
 
-/* corr_reset -- return the accumulators to the all-zero state without a readout. */
+/*
+ * corr_reset -- return the accumulators to the all-zero state without a
+ * readout (Sec. II.A: a new integration starts). Host-side bookkeeping: the
+ * handle's next call starts from zero (it stores instead of adding, after the
+ * handle's last call as always); nothing is launched, and `stream` is not
+ * used (NULL is fine).
+ */
 int corr_reset(corr_handle_t* h, void* stream);
 
 /*

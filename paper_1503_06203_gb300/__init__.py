@@ -178,7 +178,8 @@ class Correlator:
         return out
 
     def reset(self, stream=None):
-        check(lib().corr_reset(self._h, _stream_ptr(stream)))
+        # (the library orders a reset by the handle's own last call; the stream is passed through as given)
+        check(lib().corr_reset(self._h, None if stream is None else _stream_ptr(stream)))
 
     def synchronize(self, timeout_ms: int = -1):
         check(lib().corr_synchronize(self._h, timeout_ms))
@@ -270,12 +271,13 @@ def accumulate_batch(correlators, inputs, stream=None):
     """
     n = len(correlators)
     assert len(inputs) == n
-    for c, x in zip(correlators, inputs):
-        if tuple(x.shape[1:]) != (c.F_in, c.N) or not x.is_contiguous():
-            raise ValueError(f"frame shape {tuple(x.shape)} does not fit (T, F, N) with F={c.F}, N={c.N}")
+    shapes = [x.shape for x in inputs]
+    for c, x, sh in zip(correlators, inputs, shapes):
+        if len(sh) != 3 or sh[1] != c.F_in or sh[2] != c.N or not x.is_contiguous():
+            raise ValueError(f"frame shape {tuple(sh)} does not fit (T, F, N) with F={c.F}, N={c.N}")
     hs = (ctypes.c_void_p * n)(*[c._h.value for c in correlators])
     xs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in inputs])
-    Ts = (ctypes.c_int32 * n)(*[int(x.shape[0]) for x in inputs])
+    Ts = (ctypes.c_int32 * n)(*[sh[0] for sh in shapes])
     check(lib().corr_accumulate_batch_ex(hs, xs, Ts, n, _stream_ptr(stream)))
 
 
