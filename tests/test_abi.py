@@ -141,3 +141,25 @@ def test_dp4a_block_order_table_is_a_permutation():
         order = [e & 3 for e in ent]
         assert all(p not in {pl for pl, _ in planes[k]} for k, p in enumerate(order)), mk
         assert gen.pack(order) == [words[0], words[1]]
+
+
+def test_header_constants_match_the_binding():
+    """Every CORR_* constant the header defines has the same value in the Python binding."""
+    import paper_1503_06203_gb300._lib as L
+    src = open(os.path.join(ROOT, "include", "xengine.h")).read()
+    defines = dict((k, int(v)) for k, v in re.findall(r"#define (CORR_\w+) (-?\d+)", src))
+    assert "CORR_BATCH_ALONE_WAVES" in defines and "CORR_OPT_MMA_STEPS" in defines
+    for name, value in defines.items():
+        assert getattr(L, name) == value, name
+
+
+def test_batch_runs_alone_rule():
+    """A frame runs alone in a batched call from CORR_BATCH_ALONE_WAVES whole 64 x 64 tiles per SM."""
+    import paper_1503_06203_gb300 as xe
+    sms = 152
+    need = xe.CORR_BATCH_ALONE_WAVES * sms
+    for N in (1, 64, 65, 512, 1000, 2048, 8192):
+        nb = -(-N // 64)
+        per_band = nb * (nb + 1) // 2
+        F = -(-need // per_band)  # the fewest bands that reach the threshold
+        assert xe.batch_runs_alone(N, F, sms) and not (F > 1 and xe.batch_runs_alone(N, F - 1, sms)), N
