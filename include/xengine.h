@@ -169,11 +169,13 @@ int corr_reset(corr_handle_t* h, void* stream);
  * call: frame k (packed device bytes inputs[k]) is added to handle hs[k].
  * The frames' tiles share one persistent work list (Sec. II.C: tiles are
  * independent; Sec. IV: bands are independent), one correlator launch.
- * Handles must be distinct. A frame of its handle's full T whose whole tiles
- * (F x nb(nb+1)/2, nb = ceil(N/64)) number at least CORR_BATCH_ALONE_WAVES
- * per CTA slot of the GPU (one per SM) fills the GPU on its own: it is
- * launched alone, through the single-frame kernel, before the shared launch,
- * in frame order, on the same stream. Results are the same either way.
+ * Handles must be distinct. A frame whose whole tiles (F x nb(nb+1)/2,
+ * nb = ceil(N/64)) number at least CORR_BATCH_ALONE_WAVES per CTA slot of the
+ * GPU (one per SM) fills the GPU on its own: it is launched alone, through the
+ * single-frame kernel, before the shared launch, in frame order, on the same
+ * stream. That holds for a frame of its handle's full T, and for one of fewer
+ * samples (a time piece, corr_accumulate_batch_ex) where the handle's own
+ * schedule keeps tiles whole (no time split). Results are the same either way.
  */
 #define CORR_BATCH_ALONE_WAVES 4
 int corr_accumulate_batch(corr_handle_t* const* hs, const uint8_t* const* inputs, int n, void* stream);

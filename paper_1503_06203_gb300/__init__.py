@@ -264,10 +264,10 @@ def selftest_wait_timeout(polls: int = 4096, stream=None) -> int:
 def accumulate_batch(correlators, inputs, stream=None):
     """Several frames in one call: inputs[k] (device uint8 [T_k][F][N]) is added to correlators[k].
 
-    The frames share one batched launch, except that a frame of its correlator's
-    full T which fills the GPU on its own (batch_runs_alone) is launched alone
-    first, through the single-frame kernel. T_k may differ from the correlator's
-    T (frames of varying length); the correlators must be distinct.
+    The frames share one batched launch, except that a frame which fills the GPU
+    on its own (batch_runs_alone) is launched alone first, through the
+    single-frame kernel. T_k may differ from the correlator's T (frames of
+    varying length); the correlators must be distinct.
     """
     n = len(correlators)
     assert len(inputs) == n
@@ -282,7 +282,8 @@ def accumulate_batch(correlators, inputs, stream=None):
 
 
 def batch_runs_alone(N: int, F: int, sms: int) -> bool:
-    """Whether accumulate_batch launches a frame of its handle's full T alone (single-frame kernel):
-    its whole 64 x 64 tiles number at least CORR_BATCH_ALONE_WAVES per SM."""
+    """Whether accumulate_batch launches a frame of its correlator's full T alone (single-frame kernel):
+    its whole 64 x 64 tiles number at least CORR_BATCH_ALONE_WAVES per SM. A shorter frame (a time
+    piece) of such a correlator also runs alone where the correlator's schedule keeps tiles whole."""
     nb = -(-N // 64)
     return nb * (nb + 1) // 2 * F >= CORR_BATCH_ALONE_WAVES * sms

@@ -175,6 +175,9 @@ struct corr_handle {
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr}, ev_in = nullptr;
   // offset-encoded route: per-element nibble sums [F][N][2] of the current launch
   int32_t* d_sums = nullptr;
+  // a time piece's work list (batched calls that run a piece alone), grown on demand
+  int4* d_piece = nullptr;
+  int64_t piece_cap = 0;
   // corr_status: a private stream and a pinned word to read the fault word
   // after the handle's last call only (not after unrelated work)
   cudaStream_t s_status = nullptr;
@@ -779,24 +782,62 @@ int ring_set_launch(RingSet& r, int hybrid, cudaStream_t st) {
 static int batch_shared(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n,
                         cudaStream_t st);
 
-// One frame through the single-frame kernel (the body of corr_accumulate, its
-// checks done by the caller).
-static int accumulate_alone(corr_handle_t* h, const uint8_t* packed_dev, cudaStream_t st) {
+// A time piece's work list: the items of a schedule that keeps tiles whole
+// (every item starts at chunk 0), each ending at the piece's last chunk.
+__global__ void piece_items_kernel(const int4* __restrict__ src, int4* __restrict__ dst, int64_t n, int32_t nch) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < n;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int4 w = src[k];
+    w.w = nch;
+    dst[k] = w;
+  }
+}
+
+// One frame of T samples (at most the handle's T; fewer only where the
+// handle's schedule keeps its tiles whole) through the single-frame kernel:
+// the body of corr_accumulate, its checks done by the caller. A shorter frame
+// runs the handle's schedule with each item cut to its own chunks (a copy of
+// the work list rewritten on the device, after the handle's last call).
+static int accumulate_alone(corr_handle_t* h, const uint8_t* packed_dev, int32_t T, cudaStream_t st) {
   int rc = order_after_last(h, st);
   if (rc) return rc;
   const uint8_t* frame;
   int32_t np;
   int64_t row_bytes;
-  if ((rc = stage_if_needed(h, packed_dev, h->T, st, &frame, &np, &row_bytes))) return rc;
-  if ((rc = launch_frame(h, frame, np, row_bytes, h->plan, st))) return rc;
-  h->samples += h->T;
+  if ((rc = stage_if_needed(h, packed_dev, T, st, &frame, &np, &row_bytes))) return rc;
+  Plan pl = h->plan;
+  if (T != h->T) {
+    const int64_t n = pl.nitems;
+    if (h->piece_cap < n) {
+      if (h->d_piece) XE_CHECK(h, cudaFreeAsync(h->d_piece, st));
+      h->d_piece = nullptr;
+      h->piece_cap = 0;
+      cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&h->d_piece), static_cast<size_t>(n) * sizeof(int4), st);
+      if (e != cudaSuccess) {
+        h->d_piece = nullptr;
+        return alloc_failed("time-piece work list", static_cast<size_t>(n) * sizeof(int4), e);
+      }
+      h->piece_cap = n;
+    }
+    pl.T = T;
+    pl.nch = static_cast<int32_t>(ceil_div(T, xe::kTC));
+    const int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 4 * g_sms[h->device]));
+    piece_items_kernel<<<blocks, 256, 0, st>>>(h->plan.d_items, h->d_piece, n, pl.nch);
+    XE_CHECK(h, cudaGetLastError());
+    ++h->launches;
+    pl.d_items = h->d_piece;
+  }
+  if ((rc = launch_frame(h, frame, np, row_bytes, pl, st))) return rc;
+  h->samples += T;
   return record_last(h, st);
 }
 
 // Whole tiles per CTA slot from which a frame runs alone: its tiles then fill
 // every SM four times over, so it gains nothing from sharing a launch, and the
 // single-frame kernel (no frame descriptors or chunk metadata, tensor-core
-// share 5 built) runs it faster than the batched one.
+// share 5 built) runs it faster than the batched one. A frame of fewer
+// samples than its handle's T (a time piece) runs alone only where the
+// handle's schedule keeps tiles whole, so that every item stays balanced.
 constexpr int64_t kAloneWaves = CORR_BATCH_ALONE_WAVES;
 
 int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int32_t* Ts, int n, void* stream) {
@@ -819,8 +860,8 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
       if (hs[j] == hs[k]) return fail(CORR_EINVAL, "batch handles must be distinct (frames %d and %d)", j, k);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // frames that fill the GPU on their own (at their handle's T) run alone, in
-  // order, on the stream; the rest share one batched launch after them
+  // frames that fill the GPU on their own run alone, in order, on the stream;
+  // the rest share one batched launch after them
   const int64_t slots = static_cast<int64_t>(g_sms[dev]) * g_blocks_per_sm[dev];
   std::vector<corr_handle_t*> sh;
   std::vector<const uint8_t*> si;
@@ -829,8 +870,8 @@ int batch_impl(corr_handle_t* const* hs, const uint8_t* const* inputs, const int
     corr_handle* h = hs[k];
     const int32_t Tk = Ts ? Ts[k] : h->T;
     const int64_t nb = ceil_div(h->N, xe::kTile);
-    if (Tk == h->T && nb * (nb + 1) / 2 * h->F >= kAloneWaves * slots) {
-      int rc = accumulate_alone(h, inputs[k], st);
+    if (Tk <= h->T && (Tk == h->T || h->plan.split == 1) && nb * (nb + 1) / 2 * h->F >= kAloneWaves * slots) {
+      int rc = accumulate_alone(h, inputs[k], Tk, st);
       if (rc) return rc;
     } else {
       sh.push_back(h);
@@ -1629,6 +1670,7 @@ void corr_destroy(corr_handle_t* h) {
   free_plan(&h->plan_tail);
   if (h->stage) cudaFree(h->stage);
   if (h->d_sums) cudaFree(h->d_sums);
+  if (h->d_piece) cudaFree(h->d_piece);
   for (int k = 0; k < 2; ++k) {
     if (h->hchunk[k]) cudaFree(h->hchunk[k]);
     if (h->ev_copied[k]) cudaEventDestroy(h->ev_copied[k]);

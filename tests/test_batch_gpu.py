@@ -145,18 +145,25 @@ def test_batch_time_split_and_ring_reuse(xe):
 def test_batch_frames_that_fill_the_gpu_run_alone(xe):
     """Frames whose tiles fill every SM CORR_BATCH_ALONE_WAVES times run alone (single-frame kernel),
     the rest share the batched launch: every result equals the oracle, twice in a row (adds onto
-    resident sums), with the routes mixed in one call. A large frame of fewer samples than its
-    handle's T stays in the shared launch."""
+    resident sums), with the routes mixed in one call. Time pieces (fewer samples than the handle's
+    T) of such frames run alone where the handle's schedule keeps tiles whole, and share the
+    batched launch where it splits the time axis."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     big_f = -(-xe.CORR_BATCH_ALONE_WAVES * sms // 36)  # N = 512: 36 tiles per band
+    even_f = big_f  # the fewest bands from there whose tiles fill whole waves of SMs: no time split
+    while (36 * even_f) % sms:
+        even_f += 1
     shapes = [(512, big_f, 256), (64, 2, 300), (1024, -(-xe.CORR_BATCH_ALONE_WAVES * sms // 136), 128),
-              (200, 3, 1000), (512, big_f, 384)]
+              (200, 3, 1000), (512, big_f, 384), (512, even_f, 256)]
     alone = [xe.batch_runs_alone(N, F, sms) for N, F, _ in shapes]
-    assert alone == [True, False, True, False, True]
+    assert alone == [True, False, True, False, True, True]
+    split = [(np.asarray(xe.plan_schedule(N, F, T, sms)[0])[:, 2] != 0).any() for N, F, T in shapes]
+    assert not split[5] and split[4]  # piece 5 runs alone over whole tiles; piece 4 stays shared
     cors = [xe.Correlator(N, F, T) for N, F, T in shapes]
     xs = [synth.gauss(N, F, T, 2.5, 900 + k) for k, (N, F, T) in enumerate(shapes)]
-    xs[4] = np.ascontiguousarray(xs[4][:200])  # 200 of the handle's 384 samples: shared launch
+    xs[4] = np.ascontiguousarray(xs[4][:200])  # 200 of the handle's 384 samples
+    xs[5] = np.ascontiguousarray(xs[5][:200])  # 200 of 256: a ragged last chunk
     xd = [torch.from_numpy(x).cuda() for x in xs]
     for _ in range(2):
         xe.accumulate_batch(cors, xd)
