@@ -252,8 +252,8 @@ __device__ __forceinline__ void chunk_mma(uint32_t a_base, uint32_t b01_base, ui
 // changes plane between consecutive blocks where it can (dp4a_order.py
 // beside this file states the criterion and regenerates the table).
 __device__ __forceinline__ constexpr uint32_t dp4a_block(int mk, int k) {
-  return static_cast<uint32_t>(((k < 12 ? (mk == 3 ? 0x6b1c94114501841ull : 0x6b12e4288628820ull)
-                                        : 0xe7bb8d6695b4251ull) >> (5 * (k % 12))) & 31u);
+  return static_cast<uint32_t>(((k < 12 ? (mk == 3 ? 0x6b1c94114501841ull : 0x8258e4288628022ull)
+                                        : 0xef338f569a8da4dull) >> (5 * (k % 12))) & 31u);
 }
 
 template <int sel, int kMmaK, bool kEnc>
