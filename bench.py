@@ -444,16 +444,21 @@ def single_frame_record(args, wl_key, frame, peaks, rank=0, world=1, bands=None,
         c.accumulate_host(x_host)
         c.readout_async(out_host, copy_stream)
     torch.cuda.synchronize()
-    _barrier(world)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
-        c.accumulate_host(x_host)
-        c.readout_async(out_host, copy_stream)
-    stream.wait_stream(copy_stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = _max_over_ranks(world, e0.elapsed_time(e1))
+    # three timed regions of e2e_steps steps each; the median is reported (a one-off host hiccup of
+    # tens of ms inside one region would otherwise set the figure), all three are in the record
+    e2e_runs = []
+    for _ in range(3):
+        _barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            c.accumulate_host(x_host)
+            c.readout_async(out_host, copy_stream)
+        stream.wait_stream(copy_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_runs.append(_max_over_ranks(world, e0.elapsed_time(e1)))
+    e2e_ms = sorted(e2e_runs)[1]
     if not np.array_equal(out_host.numpy()[fi, xe.packed_index(N, ii, jj)].astype(np.int64), ref):
         raise RuntimeError(f"{wl_key}: end-to-end result differs from the oracle")
 
@@ -503,7 +508,9 @@ def single_frame_record(args, wl_key, frame, peaks, rank=0, world=1, bands=None,
         "e2e": {"value": round((job_ops or world * ops) * args.e2e_steps / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TOPS",
                 "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                 "h2d_gbs_measured": round(h2d_gbs, 1),
-                "ms_per_step": round(e2e_ms / args.e2e_steps, 4)},
+                "ms_per_step": round(e2e_ms / args.e2e_steps, 4),
+                "timing": f"median of 3 timed regions of {args.e2e_steps} steps",
+                "runs_ms_per_step": [round(r / args.e2e_steps, 4) for r in e2e_runs]},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "cpu_baseline": cpu_rec,
